@@ -1,0 +1,312 @@
+"""Seeded synthetic inputs: jittered triangulations and initial states.
+
+This module holds no arithmetic of the DG method.  It builds the inputs that
+both the CUDA path and the CPU oracle consume:
+
+* a structured ``nx x ny`` grid on a rectangle, each square split along a
+  seeded random diagonal, interior vertices moved by ``U(-0.2h, 0.2h)`` per
+  coordinate (boundary vertices and listed fixed points stay put);
+* counter-clockwise triangles, a periodic vertex identity map ``canon`` and a
+  per-edge boundary tag (edge ``i`` of a triangle is the edge opposite its
+  vertex ``i``, as in the paper's Fig. 1);
+* point-wise initial states in conservative variables ``(rho, m1, m2, E)``
+  for the isentropic vortex, the Sedov-type blast, the 60-degree double Mach
+  reflection and the four-quadrant Riemann problem.
+
+Projection of a point-wise state onto the modal basis is method arithmetic
+and lives on each side of the boundary separately.
+
+The paper's EasyMesh meshes are not available; these jittered grids stand in
+for them.  Random numbers come from numpy's PCG64 generator with the seed
+recorded by the caller.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# Boundary tags of an edge without a neighbour (an interface shared with the
+# C ABI; the numeric values are fixed there).
+BC_NONE = 0          # must have a neighbour (interior or periodic via canon)
+BC_REFLECT = 1
+BC_TRANSMISSIVE = 2
+BC_DIRICHLET0 = 3    # constant states 0..3 -> tags 3..6
+BC_SHOCK = 7         # moving oblique shock (double Mach reflection top wall)
+
+GAMMA = 1.4
+
+
+@dataclass
+class Mesh:
+    xy: np.ndarray            # float64 [nv, 2]
+    tri: np.ndarray           # int32 [nt, 3], counter-clockwise
+    canon: np.ndarray         # int32 [nv]
+    bc: np.ndarray            # int8 [nt, 3], tag of the edge opposite vertex i
+    nx: int = 0
+    ny: int = 0
+    box: tuple = (0.0, 1.0, 0.0, 1.0)
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def nv(self) -> int:
+        return int(self.xy.shape[0])
+
+    @property
+    def nt(self) -> int:
+        return int(self.tri.shape[0])
+
+
+def jittered_grid(nx: int, ny: int, box=(0.0, 1.0, 0.0, 1.0), seed: int = 0,
+                  jitter: float = 0.2, periodic: bool = False,
+                  fixed_points=(), side_tags=None) -> Mesh:
+    """Jittered structured triangulation of ``box = (x0, x1, y0, y1)``.
+
+    ``side_tags`` maps a side name ('left', 'right', 'bottom', 'top') to a
+    boundary tag or to a callable ``f(xmid, ymid) -> tag`` evaluated at the
+    edge midpoint.  With ``periodic=True`` opposite sides are identified
+    through ``canon`` and no side tags are needed.
+    """
+    if nx < 2 or ny < 2:
+        raise ValueError("need nx, ny >= 2")
+    x0, x1, y0, y1 = box
+    hx = (x1 - x0) / nx
+    hy = (y1 - y0) / ny
+    rng = np.random.default_rng(seed)
+    ii, jj = np.meshgrid(np.arange(nx + 1), np.arange(ny + 1), indexing="xy")
+    ii = ii.reshape(-1)
+    jj = jj.reshape(-1)
+    xy = np.stack([x0 + ii * hx, y0 + jj * hy], axis=1).astype(np.float64)
+    interior = (ii > 0) & (ii < nx) & (jj > 0) & (jj < ny)
+    for (px, py) in fixed_points:
+        hit = (np.abs(xy[:, 0] - px) < 1e-12 * max(1.0, abs(px))) & \
+              (np.abs(xy[:, 1] - py) < 1e-12 * max(1.0, abs(py)))
+        interior &= ~hit
+    dj = rng.uniform(-jitter, jitter, size=(xy.shape[0], 2))
+    dj[~interior] = 0.0
+    xy[:, 0] += dj[:, 0] * hx
+    xy[:, 1] += dj[:, 1] * hy
+
+    def vid(i, j):
+        return j * (nx + 1) + i
+
+    qi, qj = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")
+    qi = qi.reshape(-1)
+    qj = qj.reshape(-1)
+    v00 = vid(qi, qj)
+    v10 = vid(qi + 1, qj)
+    v01 = vid(qi, qj + 1)
+    v11 = vid(qi + 1, qj + 1)
+    diag = rng.integers(0, 2, size=qi.shape[0])
+    tri = np.empty((2 * qi.shape[0], 3), dtype=np.int32)
+    a = diag == 0
+    # diagonal v00-v11: (v00, v10, v11), (v00, v11, v01)
+    tri[0::2][a] = np.stack([v00[a], v10[a], v11[a]], axis=1)
+    tri[1::2][a] = np.stack([v00[a], v11[a], v01[a]], axis=1)
+    b = ~a
+    # diagonal v10-v01: (v00, v10, v01), (v10, v11, v01)
+    tri[0::2][b] = np.stack([v00[b], v10[b], v01[b]], axis=1)
+    tri[1::2][b] = np.stack([v10[b], v11[b], v01[b]], axis=1)
+
+    if periodic:
+        canon = (jj % ny) * (nx + 1) + (ii % nx)
+    else:
+        canon = np.arange(xy.shape[0])
+    canon = canon.astype(np.int32)
+
+    bc = np.zeros(tri.shape, dtype=np.int8)
+    if not periodic:
+        side_tags = side_tags or {}
+        # edge e opposite local vertex e joins local vertices e+1, e+2
+        for e in range(3):
+            va = tri[:, (e + 1) % 3]
+            vb = tri[:, (e + 2) % 3]
+            ia, ja = ii[va], jj[va]
+            ib, jb = ii[vb], jj[vb]
+            xm = 0.5 * (xy[va, 0] + xy[vb, 0])
+            ym = 0.5 * (xy[va, 1] + xy[vb, 1])
+            for side, sel in (("left", (ia == 0) & (ib == 0)),
+                              ("right", (ia == nx) & (ib == nx)),
+                              ("bottom", (ja == 0) & (jb == 0)),
+                              ("top", (ja == ny) & (jb == ny))):
+                if not sel.any():
+                    continue
+                tag = side_tags.get(side, BC_TRANSMISSIVE)
+                if callable(tag):
+                    bc[sel, e] = np.asarray([tag(x, y) for x, y in zip(xm[sel], ym[sel])],
+                                            dtype=np.int8)
+                else:
+                    bc[sel, e] = tag
+    return Mesh(xy=xy, tri=tri, canon=canon, bc=bc, nx=nx, ny=ny, box=tuple(box),
+                meta={"seed": seed, "jitter": jitter, "periodic": periodic})
+
+
+# ----------------------------------------------------------------------------
+# Point-wise initial states (conservative variables), vectorised over points.
+# ----------------------------------------------------------------------------
+
+def prim_to_cons(rho, u, v, p, gamma=GAMMA):
+    rho = np.asarray(rho, dtype=np.float64)
+    u = np.asarray(u, dtype=np.float64)
+    v = np.asarray(v, dtype=np.float64)
+    p = np.asarray(p, dtype=np.float64)
+    E = p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v)
+    return np.stack(np.broadcast_arrays(rho, rho * u, rho * v, E), axis=-1)
+
+
+def vortex_state(x, y, t=0.0, strength=5.0, radius=0.1, center=(0.5, 0.5),
+                 background=(1.0, 1.0, 1.0, 1.0), box=(0.0, 1.0, 0.0, 1.0),
+                 gamma=GAMMA, images=1):
+    """Isentropic vortex advected by the background flow on a periodic box.
+
+    The classic vortex on [-5, 5]^2 mapped to a radius scale ``radius``:
+    with r' = |x - x_c(t)| / radius,
+    dv = strength/(2 pi) exp((1 - r'^2)/2) (-y', x'),
+    T = 1 - (gamma-1) strength^2 / (8 gamma pi^2) exp(1 - r'^2),
+    rho = T^(1/(gamma-1)), p = rho T  (for rho_inf = p_inf = 1).
+    Periodic images within ``images`` box lengths are summed in the velocity
+    and temperature perturbations.
+    """
+    rho0, u0, v0, p0 = background
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    Lx = box[1] - box[0]
+    Ly = box[3] - box[2]
+    cx = box[0] + ((center[0] + u0 * t - box[0]) % Lx)
+    cy = box[2] + ((center[1] + v0 * t - box[2]) % Ly)
+    du = np.zeros_like(x)
+    dv = np.zeros_like(x)
+    dT = np.zeros_like(x)
+    for a in range(-images, images + 1):
+        for b in range(-images, images + 1):
+            xr = (x - (cx + a * Lx)) / radius
+            yr = (y - (cy + b * Ly)) / radius
+            r2 = xr * xr + yr * yr
+            f = strength / (2.0 * math.pi) * np.exp(0.5 * (1.0 - r2))
+            du += -yr * f
+            dv += xr * f
+            dT += -(gamma - 1.0) * strength ** 2 / (8.0 * gamma * math.pi ** 2) * np.exp(1.0 - r2)
+    T = p0 / rho0 + dT
+    rho = rho0 * (T / (p0 / rho0)) ** (1.0 / (gamma - 1.0))
+    p = rho * T
+    return prim_to_cons(rho, u0 + du, v0 + dv, p, gamma)
+
+
+def dmr_states(gamma=GAMMA):
+    """Post- and pre-shock states of the Mach-10 double Mach reflection.
+
+    The post-shock velocity (8.25 along the shock normal) is split with the
+    shock inclined at 60 degrees to the x-axis: (8.25 cos30, -8.25 sin30).
+    """
+    post = prim_to_cons(8.0, 8.25 * math.cos(math.pi / 6), -8.25 * math.sin(math.pi / 6), 116.5, gamma)
+    pre = prim_to_cons(1.4, 0.0, 0.0, 1.0, gamma)
+    return post.reshape(4), pre.reshape(4)
+
+
+# ----------------------------------------------------------------------------
+# Workload recipes (mesh + point-wise initial state + configuration)
+# ----------------------------------------------------------------------------
+
+@dataclass
+class Workload:
+    name: str
+    mesh: Mesh
+    k: int
+    t_end: float
+    u0: object                 # callable (x, y) -> [.., 4] conservative state
+    cell_u0: object = None     # optional callable (cell ids) -> [.., 4] piecewise-constant state
+    bc_state: np.ndarray = field(default_factory=lambda: np.zeros((4, 4)))
+    shock: tuple = (0.0, 0.0, 0.0, 0, 0)   # x0, angle, speed, pre index, post index
+    gamma: float = GAMMA
+
+
+def vortex_workload(n=32, k=1, seed=1, radius=0.1, t_end=0.5, strength=5.0):
+    mesh = jittered_grid(n, n, (0.0, 1.0, 0.0, 1.0), seed=seed, periodic=True)
+    return Workload(name=f"vortex{n}x{n}_P{k}", mesh=mesh, k=k, t_end=t_end,
+                    u0=lambda x, y: vortex_state(x, y, 0.0, strength=strength, radius=radius))
+
+
+def sedov_workload(n=256, k=2, seed=2, t_end=1.0, energy=0.244816, p_floor=1e-10):
+    L = 1.1
+    mesh = jittered_grid(n, n, (-L, L, -L, L), seed=seed, fixed_points=[(0.0, 0.0)],
+                         side_tags={s: BC_REFLECT for s in ("left", "right", "bottom", "top")})
+    xy = mesh.xy
+    origin = np.argmin(xy[:, 0] ** 2 + xy[:, 1] ** 2)
+    touch = np.any(mesh.tri == origin, axis=1)
+    x0 = xy[mesh.tri[:, 0]]
+    x1 = xy[mesh.tri[:, 1]]
+    x2 = xy[mesh.tri[:, 2]]
+    area = 0.5 * ((x1[:, 0] - x0[:, 0]) * (x2[:, 1] - x0[:, 1]) - (x2[:, 0] - x0[:, 0]) * (x1[:, 1] - x0[:, 1]))
+    p_blast = (GAMMA - 1.0) * energy / area[touch].sum()
+    p_cell = np.where(touch, p_blast, p_floor)
+    cons = prim_to_cons(np.ones(mesh.nt), np.zeros(mesh.nt), np.zeros(mesh.nt), p_cell)
+
+    def cell_u0(cells):
+        return cons[np.asarray(cells)]
+    return Workload(name=f"sedov{n}x{n}_P{k}", mesh=mesh, k=k, t_end=t_end,
+                    u0=None, cell_u0=cell_u0)
+
+
+def dmr_workload(nx=1440, ny=360, k=2, seed=3, t_end=0.2):
+    post, pre = dmr_states()
+    x0 = 1.0 / 6.0
+    bottom = lambda x, y: BC_DIRICHLET0 if x < x0 else BC_REFLECT
+    mesh = jittered_grid(nx, ny, (0.0, 4.0, 0.0, 1.0), seed=seed,
+                         side_tags={"left": BC_DIRICHLET0, "right": BC_TRANSMISSIVE,
+                                    "bottom": bottom, "top": BC_SHOCK})
+    bc_state = np.zeros((4, 4))
+    bc_state[0] = post
+    bc_state[1] = pre
+    s3 = math.sqrt(3.0)
+
+    def u0(x, y):
+        x = np.asarray(x, dtype=np.float64)
+        y = np.asarray(y, dtype=np.float64)
+        behind = x < x0 + y / s3
+        return np.where(behind[..., None], post, pre)
+    return Workload(name=f"dmr{nx}x{ny}_P{k}", mesh=mesh, k=k, t_end=t_end, u0=u0,
+                    bc_state=bc_state, shock=(x0, math.pi / 3.0, 10.0, 1, 0))
+
+
+def riemann4_workload(n=64, k=1, seed=4, t_end=0.2):
+    rng = np.random.default_rng(seed + 1000)
+    rho = rng.uniform(0.1, 2.0, 4)
+    p = rng.uniform(0.01, 2.0, 4)
+    u = rng.uniform(-1.0, 1.0, 4)
+    v = rng.uniform(-1.0, 1.0, 4)
+    states = prim_to_cons(rho, u, v, p)
+    mesh = jittered_grid(n, n, (0.0, 1.0, 0.0, 1.0), seed=seed,
+                         side_tags={s: BC_TRANSMISSIVE for s in ("left", "right", "bottom", "top")})
+
+    def u0(x, y):
+        x = np.asarray(x, dtype=np.float64)
+        y = np.asarray(y, dtype=np.float64)
+        q = (x >= 0.5).astype(int) + 2 * (y >= 0.5).astype(int)
+        return states[q]
+    return Workload(name=f"riemann4_{n}x{n}_P{k}", mesh=mesh, k=k, t_end=t_end, u0=u0)
+
+
+def uniform_workload(n=16, k=2, seed=5, state=(1.0, 0.3, -0.2, 2.5), periodic=True):
+    mesh = jittered_grid(n, n, (0.0, 1.0, 0.0, 1.0), seed=seed, periodic=periodic,
+                         side_tags=None if periodic else
+                         {s: BC_TRANSMISSIVE for s in ("left", "right", "bottom", "top")})
+    st = np.asarray(state, dtype=np.float64)
+    return Workload(name=f"uniform{n}_P{k}", mesh=mesh, k=k, t_end=0.1,
+                    u0=lambda x, y: np.broadcast_to(st, np.shape(x) + (4,)).copy())
+
+
+def random_modal_state(nt: int, k: int, seed: int, mean=(1.0, 0.2, -0.1, 2.5),
+                       amp=0.05, mean_jitter=0.1):
+    """Random modal coefficients [4][nb][nt] with a positive mean state.
+
+    Used for parity tests only (a perturbation of a constant state, so that
+    density and pressure stay positive at every point).
+    """
+    nb = 3 if k == 1 else 6
+    rng = np.random.default_rng(seed)
+    u = np.zeros((4, nb, nt))
+    mean = np.asarray(mean, dtype=np.float64)
+    u[:, 0, :] = mean[:, None] * (1.0 + mean_jitter * rng.uniform(-1, 1, (4, nt)))
+    u[:, 1:, :] = amp * np.abs(mean)[:, None, None] * rng.uniform(-1, 1, (4, nb - 1, nt))
+    return u

@@ -1,0 +1,157 @@
+"""Whole-step pins of the oracle's BP RI-OEDG scheme (Sec. 4.5): free stream,
+conservation, rotation and evolution invariance, bound preservation and
+design order on smooth exact solutions."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2409_09620_gb300 import workloads as W
+from tests.helpers import rotate_mesh_state
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_free_stream_steps(oracle_mod, k):
+    O = oracle_mod
+    wl = W.uniform_workload(n=8, k=k)
+    om = O.OracleMesh.from_mesh(wl.mesh)
+    u0 = O.project_workload(om, wl)
+    u, t, cnt, rc = om.advance(O.config_for(wl), u0, 0.0, 1.0, max_steps=10)
+    assert rc == 0 and cnt[3] == 10
+    assert np.abs(u - u0).max() < 1e-13 * np.abs(u0).max()
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_conservation_with_oe_and_limiter(oracle_mod, k):
+    """OE keeps mode 0 and the limiter keeps averages: sum |K| u_K is conserved
+    on a periodic mesh through full steps."""
+    O = oracle_mod
+    wl = W.riemann4_workload(n=10, k=k)
+    mesh = W.jittered_grid(10, 10, seed=60, periodic=True)
+    om = O.OracleMesh.from_mesh(mesh)
+    u0 = om.project(k, fn=wl.u0)
+    cf = O.make_config(k)
+    u0, _ = om.limit(cf, u0)
+    area, _, _ = om.geometry()
+    u, t, cnt, rc = om.advance(cf, u0, 0.0, 10.0, max_steps=15)
+    assert rc == 0
+    m0 = (u0[:, 0] * area).sum(1)
+    m1 = (u[:, 0] * area).sum(1)
+    assert (np.abs(m1 - m0) <= 1e-13 * (np.abs(u0[:, 0]) * area).sum(1)).all()
+    # reflecting walls conserve mass and energy; the limiter is active on the blast
+    wl = W.sedov_workload(n=12, k=k)
+    om = O.OracleMesh.from_mesh(wl.mesh)
+    cf = O.config_for(wl)
+    u0 = O.project_workload(om, wl)
+    area, _, _ = om.geometry()
+    u, t, cnt, rc = om.advance(cf, u0, 0.0, 10.0, max_steps=15)
+    assert rc == 0 and cnt[0] > 0
+    for c in (0, 3):
+        m0 = (u0[c, 0] * area).sum()
+        assert abs((u[c, 0] * area).sum() - m0) <= 1e-13 * abs(m0)
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_step_rotation_invariance(oracle_mod, k):
+    """RI-OEDG is rotation invariant (Thm Rotational Invariance; RI-error test of
+    the implosion example): rotate the mesh and state by pi/4, run 5 steps,
+    rotate back.  The component-wise OE (CW-OEDG) shows a far larger error."""
+    O = oracle_mod
+    wl = W.riemann4_workload(n=10, k=k)
+    mesh = W.jittered_grid(10, 10, seed=61, periodic=True)
+    om = O.OracleMesh.from_mesh(mesh)
+    u0 = om.project(k, fn=wl.u0)
+    err = {}
+    for oe in (1, 2):
+        cf = O.make_config(k, oe=oe)
+        u0l, _ = om.limit(cf, u0)
+        u, _, _, _ = om.advance(cf, u0l, 0.0, 10.0, max_steps=5)
+        xy, ur0 = rotate_mesh_state(mesh, u0l, math.pi / 4)
+        omr = O.OracleMesh(xy, mesh.tri, mesh.canon, mesh.bc)
+        ur, _, _, _ = omr.advance(cf, ur0, 0.0, 10.0, max_steps=5)
+        _, ur_back = rotate_mesh_state(mesh, ur, -math.pi / 4)
+        err[oe] = np.abs(ur_back - u).max() / np.abs(u).max()
+    assert err[1] < 1e-12
+    assert err[2] > 1e3 * max(err[1], 1e-16)
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_evolution_invariance(oracle_mod, k):
+    """Sec. 2.4 evolution invariance through the Euler similarity
+    (rho, v, p) -> (rho, 2v, 4p): same density after the same number of steps
+    of half the size, momentum doubled, energy quadrupled (power-of-two scalings
+    are exact in binary)."""
+    O = oracle_mod
+    wl = W.riemann4_workload(n=8, k=k)
+    om = O.OracleMesh.from_mesh(wl.mesh)
+    cf = O.config_for(wl)
+    u0 = O.project_workload(om, wl)
+    lam = np.array([1.0, 2.0, 2.0, 4.0])[:, None, None]
+    u, t, _, _ = om.advance(cf, u0, 0.0, 10.0, max_steps=6)
+    ul, tl, _, _ = om.advance(cf, u0 * lam, 0.0, 10.0, max_steps=6)
+    np.testing.assert_allclose(tl, t / 2, rtol=1e-14)
+    assert np.abs(ul / lam - u).max() < 1e-13 * np.abs(u).max()
+
+
+def test_bound_preservation_sedov(oracle_mod):
+    """Thm 4.3 / Cor. 4.5: with the BP limiter after every stage, density and
+    internal energy are positive at every point of the decomposition set and
+    no cell average leaves G, on a near-vacuum blast (p = 1e-10)."""
+    O = oracle_mod
+    wl = W.sedov_workload(n=16, k=2)
+    om = O.OracleMesh.from_mesh(wl.mesh)
+    cf = O.config_for(wl)
+    u = O.project_workload(om, wl)
+    t = 0.0
+    for s in range(12):
+        u, t, dt, cnt, rc = om.step(cf, u, t, 1.0)
+        assert rc == 0 and cnt[1] == 0
+        mins = om.point_minima(cf, u)
+        assert (mins > 0).all()
+    assert cnt[0] >= 0
+
+
+def density_wave(x, y, t=0.0):
+    rho = 1.0 + 0.2 * np.sin(2 * np.pi * (x + y - 2 * t))    # advected by v = (1, 1)
+    return W.prim_to_cons(rho, 1.0 + 0 * x, 1.0 + 0 * x, 1.0 + 0 * x)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("k,ns", [(1, (8, 16, 32)), (2, (16, 32, 64))])
+def test_design_order_density_wave(oracle_mod, k, ns):
+    """P^k DG with RIOE + BP keeps (k+1)-th order on a smooth exact solution
+    (cf. the paper's accuracy tables)."""
+    O = oracle_mod
+    errs = []
+    t_end = 0.1
+    for n in ns:
+        mesh = W.jittered_grid(n, n, seed=70, periodic=True)
+        om = O.OracleMesh.from_mesh(mesh)
+        cf = O.make_config(k)
+        u0 = om.project(k, fn=density_wave)
+        u, t, _, rc = om.advance(cf, u0, 0.0, t_end)
+        assert rc == 0 and t == t_end
+        ex = om.project(k, fn=lambda x, y: density_wave(x, y, t_end))
+        area, _, _ = om.geometry()
+        errs.append((np.abs(u[0, 0] - ex[0, 0]) * area).sum())
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    assert rates[-1] > k + 1 - 0.3, (errs, rates)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("k,ns", [(1, (16, 32, 64)), (2, (16, 32))])
+def test_vortex_converges(oracle_mod, k, ns):
+    """Isentropic vortex (strength 5): the error falls at close to design order."""
+    O = oracle_mod
+    errs = []
+    for n in ns:
+        wl = W.vortex_workload(n=n, k=k, t_end=0.05)
+        om = O.OracleMesh.from_mesh(wl.mesh)
+        cf = O.config_for(wl)
+        u0 = om.project(k, fn=wl.u0)
+        u, t, _, rc = om.advance(cf, u0, 0.0, wl.t_end)
+        ex = om.project(k, fn=lambda x, y: W.vortex_state(x, y, wl.t_end))
+        area, _, _ = om.geometry()
+        errs.append((np.abs(u[0, 0] - ex[0, 0]) * area).sum())
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    assert rates[-1] > k + 1 - 0.5, (errs, rates)
