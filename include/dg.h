@@ -1,0 +1,190 @@
+/*
+ * dg.h -- C ABI of the GB300 (sm_103a) BP RI-OEDG solver for the 2D Euler
+ * equations with P1/P2 modal DG on triangles.
+ *
+ * Method: Ding, Cui & Wu, "Robust DG Schemes on Unstructured Triangular
+ * Meshes: Oscillation Elimination and Bound Preservation via Optimal Convex
+ * Decomposition" (arXiv 2409.09620).  Section / equation labels below refer
+ * to that paper.
+ *
+ * Conventions shared by every call:
+ *  - All functions return int32_t status: DG_OK (0) or a negative DG_E* code;
+ *    dg_last_error() returns a thread-local message for the last failure.
+ *  - Pointers named host_* or documented as "host" are host memory; the
+ *    library copies what it needs and never keeps a caller pointer.
+ *  - The library owns every handle and every device allocation behind it.
+ *  - A modal state is double coeffs[(c * nb + l) * nt + K]: component c in
+ *    (rho, m1, m2, E), mode l in 0..nb-1 (nb = 3 for P1, 6 for P2, basis of
+ *    eq. basisfunc, vertex v1 of each triangle is the origin of the
+ *    reference map), cell K in 0..nt-1.
+ *  - Triangles are counter-clockwise; local edge i is the edge opposite local
+ *    vertex i (Fig. 1: e3 joins v1 and v2).
+ */
+#ifndef DG_GB300_H
+#define DG_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define DG_OK 0
+#define DG_EINVAL (-1)    /* bad argument */
+#define DG_EMESH (-2)     /* invalid mesh: area <= 0, non-manifold, unmatched edge */
+#define DG_ENOMEM (-3)    /* host or device allocation failed */
+#define DG_ENONPHYS (-4)  /* a cell average left the admissible set G (eq. G:Euler) */
+#define DG_ECUDA (-5)     /* CUDA runtime error */
+#define DG_ETIMEOUT (-6)  /* a bounded device wait ran out */
+#define DG_EBUSY (-7)     /* resource busy */
+
+/* boundary tags for edges without a neighbour (bc[3 * K + i]) */
+#define DG_BC_NONE 0          /* must have a neighbour (interior, or periodic via canon) */
+#define DG_BC_REFLECT 1       /* mirror state (solid wall) */
+#define DG_BC_TRANSMISSIVE 2  /* exterior state = interior trace */
+#define DG_BC_DIRICHLET0 3    /* 3..6: constant state cfg.bc_state[tag - 3] */
+#define DG_BC_SHOCK 7         /* moving oblique shock: post state behind, pre state ahead */
+
+/* configuration values */
+#define DG_PREC_FP64 0        /* every operation in FP64 */
+#define DG_PREC_MIXED 1       /* FP32 modes and flux arithmetic; FP64 cell averages and limiter */
+#define DG_OE_OFF 0
+#define DG_OE_RI 1            /* rotation-invariant OE (Sec. 3.3) */
+#define DG_OE_CW 2            /* component-wise OE (Sec. 3.2) */
+#define DG_BP_OFF 0
+#define DG_BP_ON 1            /* simplified BP limiter at the decomposition points (Sec. 4.4) */
+#define DG_DECOMP_OPTIMAL 0   /* optimal convex decomposition (Sec. 4.2) and its CFL */
+#define DG_DECOMP_ZXS 1       /* classical Zhang-Xia-Shu decomposition and its CFL */
+
+typedef struct dg_mesh dg_mesh;
+typedef struct dg_solver dg_solver;
+
+typedef struct dg_config {
+  int32_t k;              /* polynomial degree: 1 or 2 */
+  int32_t precision;      /* DG_PREC_* */
+  int32_t oe;             /* DG_OE_* */
+  int32_t bp;             /* DG_BP_* */
+  int32_t decomp;         /* DG_DECOMP_* */
+  int32_t reserved;       /* set to 0 */
+  double gamma;           /* adiabatic index (1.4 in Sec. 5.3) */
+  double cfl;             /* multiplies the BP time step of Sec. 5 (1.0 = the paper's step) */
+  double bc_state[4][4];  /* conservative Dirichlet states for tags 3..6 */
+  double shock_x0;        /* moving shock: its line meets y = 0 at x = shock_x0 at t = 0 */
+  double shock_angle;     /* angle of the shock line to the x-axis (radians) */
+  double shock_speed;     /* speed of the shock along its normal */
+  int32_t shock_pre;      /* index into bc_state of the state ahead of the shock */
+  int32_t shock_post;     /* index into bc_state of the state behind the shock */
+} dg_config;
+
+typedef struct dg_stats {
+  int64_t steps;          /* time steps taken by the call */
+  int64_t limited_cells;  /* cell-stages with a limiter scaling theta < 1 */
+  int64_t nonphysical;    /* cell-stages whose average left G before limiting */
+  int64_t cfl_breaches;   /* stages whose alpha * dt exceeded min C_K |K| (reading of eq. 1009) */
+  double t;               /* time reached */
+  double dt_last;         /* last step size */
+  double alpha;           /* viscosity coefficient (eq. 1250) of the current state */
+} dg_stats;
+
+/* ---------------------------------------------------------------------- */
+/* Mesh (Sec. 2 notation; Sec. 4.2 decomposition)                          */
+/* ---------------------------------------------------------------------- */
+
+/* Build a mesh from host arrays: xy[2 * nv] vertex coordinates, tri[3 * nt]
+ * counter-clockwise vertex ids, canon[nv] periodic vertex identity (NULL =
+ * identity: vertices with equal canon are the same point of a periodic
+ * domain), bc[3 * nt] boundary tags of edges without a neighbour (NULL = all
+ * DG_BC_NONE).  Computes the neighbour of every edge on the host and the
+ * per-cell geometry and optimal convex decomposition (eqs. 1040, 1139) on the
+ * GPU.  Errors: DG_EINVAL (nt <= 0, nv <= 0, NULL arrays), DG_EMESH (vertex id
+ * out of range, area <= 0, an edge shared by more than two cells or traversed
+ * twice in the same direction, a boundary edge tagged DG_BC_NONE), DG_ENOMEM,
+ * DG_ECUDA.  *out receives a handle owned by the caller (dg_mesh_destroy). */
+int32_t dg_mesh_create(int64_t nv, const double *xy, int64_t nt, const int32_t *tri,
+                       const int32_t *canon, const int8_t *bc, dg_mesh **out);
+void dg_mesh_destroy(dg_mesh *mesh);
+/* number of cells; min over cells of C_{K,k} |K| (eqs. 1692, 1713, or the ZXS
+ * numbers when decomp = DG_DECOMP_ZXS) for k = 1 and 2 */
+int32_t dg_mesh_info(const dg_mesh *mesh, int32_t decomp, int64_t *nt, double *min_cfl_area_p1,
+                     double *min_cfl_area_p2);
+/* host copies of the adjacency: nbr[3 * nt] (-1 on a boundary) and the
+ * neighbour's local edge nbr_edge[3 * nt] (-1 on a boundary) */
+int32_t dg_mesh_neighbors(const dg_mesh *mesh, int32_t *nbr, int32_t *nbr_edge);
+/* host copies of the device geometry for degree k: area[nt], len[3 * nt],
+ * normal[6 * nt] (per cell and edge: nx, ny), c_area[nt] = C_{K,k} |K| of the
+ * chosen decomposition, nodes[4 * nt] = reference coordinates (xi, eta) of the
+ * two P2 internal nodes (eq. 1139), limv[2 * nt] = local ids of the P1
+ * limiter vertices v1, v2 (opposite the longest and second-longest edges) */
+int32_t dg_mesh_geometry(const dg_mesh *mesh, int32_t k, int32_t decomp, double *area, double *len,
+                         double *normal, double *c_area, double *nodes, int8_t *limv);
+
+/* physical points of the 12-point rule (Appendix A, Table tab:6th):
+ * xy[(K * 12 + mu) * 2 + d] (host) */
+int32_t dg_quad_points(const dg_mesh *mesh, double *xy);
+/* L2 projection onto P^k with the 12-point rule: vals[(K * 12 + mu) * 4 + c]
+ * are conservative point values at dg_quad_points (host); coeffs is a host
+ * modal state (layout above) */
+int32_t dg_project(const dg_mesh *mesh, int32_t k, const double *vals, double *coeffs);
+
+/* ---------------------------------------------------------------------- */
+/* Solver: the SSP-RK3 BP RI-OEDG scheme of Sec. 4.5                        */
+/* ---------------------------------------------------------------------- */
+
+/* Create a solver on `mesh` (the mesh must outlive it) with host initial
+ * coefficients; applies the BP limiter once (the theorems assume the
+ * solution at t^n satisfies eq. 1526), computes alpha and captures one SSP-RK3
+ * step as a CUDA graph on `cuda_stream` (a cudaStream_t, or NULL for a
+ * stream the solver creates).  Time starts at 0.  Errors: DG_EINVAL,
+ * DG_ENONPHYS (an initial cell average is not in G), DG_ENOMEM, DG_ECUDA. */
+int32_t dg_init(const dg_mesh *mesh, const dg_config *cfg, const double *coeffs, void *cuda_stream,
+                dg_solver **out);
+/* Advance until t >= t_end or max_steps steps, with dt from the BP CFL
+ * condition (Sec. 5: dt = cfl * min_K C_K |K| / alpha, clamped to t_end).
+ * Blocks until done.  stats may be NULL.  Returns DG_ENONPHYS if any cell
+ * average left G during the call (the state is still advanced). */
+int32_t dg_advance(dg_solver *solver, double t_end, int64_t max_steps, dg_stats *stats);
+/* Enqueue exactly n steps (t_end = +inf) on the solver's stream and return
+ * without synchronising; pair with dg_sync.  For device-side timing. */
+int32_t dg_advance_async(dg_solver *solver, int64_t n);
+int32_t dg_sync(dg_solver *solver, dg_stats *stats);
+/* host copy of the current state (len = number of doubles available in
+ * coeffs, at least 4 * nb * nt) and time (t may be NULL) */
+int32_t dg_get_state(const dg_solver *solver, double *coeffs, size_t len, double *t);
+/* replace the state (host coefficients, used as given, not limited) and time */
+int32_t dg_set_state(dg_solver *solver, const double *coeffs, double t);
+/* the solver's CUDA stream (cudaStream_t) */
+void *dg_stream(const dg_solver *solver);
+void dg_solver_destroy(dg_solver *solver);
+
+/* ---------------------------------------------------------------------- */
+/* Single operators of one stage, on host buffers (for verification).      */
+/* Each runs the same kernels as dg_advance on the solver's mesh/config.    */
+/* ---------------------------------------------------------------------- */
+
+/* u_h = a * un + b * (v + dt * L(v)) with the LF viscosity alpha and
+ * boundary time t (eqs. DGSystem:Dis, RKTime) */
+int32_t dg_op_rk_stage(dg_solver *solver, const double *un, const double *v, double a, double b,
+                       double dt, double alpha, double t, double *uh);
+/* global OE statistics of u (eqs. normOmg, RIOESys:Coef1): stats[0..3]
+ * domain means, [4] sup |rho - mean|, [5] sup |m - mean m|, [6] sup |E - mean|,
+ * [7] |Omega|, [8] sup |m1 - mean|, [9] sup |m2 - mean| */
+int32_t dg_op_stats(dg_solver *solver, const double *u, double *stats);
+/* OE procedure (eq. oe:sys with the RIOE coefficients) with the given stats;
+ * the limiter is not applied; t is the time of boundary ghost states */
+int32_t dg_op_oe(dg_solver *solver, const double *u, double dt, const double *stats, double t,
+                 double *out);
+/* BP limiter (Sec. 4.4); counters[0] += limited cells, counters[1] +=
+ * cells with an average outside G */
+int32_t dg_op_limit(dg_solver *solver, const double *u, double *out, int64_t *counters);
+/* viscosity coefficient alpha of u at time t (eq. 1250) */
+int32_t dg_op_alpha(dg_solver *solver, const double *u, double t, double *alpha);
+
+/* thread-local message of the last error */
+const char *dg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

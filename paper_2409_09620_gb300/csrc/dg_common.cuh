@@ -1,0 +1,215 @@
+// dg_common.cuh -- device data layout, basis, quadrature and physics of the
+// GB300 BP RI-OEDG solver (Ding, Cui & Wu, arXiv 2409.09620).
+//
+// Data layout in HBM (one mesh of nt cells):
+//   state     avg[4][nt] (FP64 cell averages, mode 0)  +  hi[4][nb-1][nt] (modes 1..nb-1, Real)
+//   geometry  area[nt], jinv[4][nt] (dxi/dx, dxi/dy, deta/dx, deta/dy), nrm[6][nt],
+//             len[3][nt], vxy[6][nt], node[4][nt] (P2 internal nodes, reference coords),
+//             limv[2][nt] (P1 limiter vertices), conn[3][nt] (neighbour << 2 | its edge, or -tag)
+//   exchange  tr[nt][3][Q][8]  traces of the stage input at edge Gauss points:
+//                              u (4) and F(u).n_i (4), written by the cell that owns them
+//             vd[nt][3][12]    value (4) and physical gradient (8) of u_h at each vertex
+//             hs[nt][12]       physical Hessian (xx, xy, yy) of u_h per component (P2)
+// Every kernel is one thread per cell; reductions are per-block partials
+// reduced in a fixed order, so results are bitwise reproducible.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dg {
+
+constexpr int TPB = 128;                 // cells per block
+constexpr int FIN_THREADS = 256;         // threads of the finalize kernels
+
+template <int K> struct Deg;
+template <> struct Deg<1> { static constexpr int NB = 3, NQ = 2, NV = 3; };
+template <> struct Deg<2> { static constexpr int NB = 6, NQ = 3, NV = 6; };
+
+struct MeshDev {
+  int64_t nt;
+  const double *area, *jinv, *nrm, *len, *vxy, *node;
+  const int8_t *limv;
+  const int32_t *conn;
+};
+
+template <typename Real> struct StateDev {
+  double *avg;   // [4][nt]
+  Real *hi;      // [4][nb-1][nt]
+};
+
+struct Phys {
+  double gamma;
+  double bc[4][4];
+  double shock_x0, shock_cot, shock_vx;   // x_s(y, t) = x0 + y cot(angle) + t speed / sin(angle)
+  int shock_pre, shock_post;
+  int oe, bp, k, pad;
+};
+
+// Device-resident scalars of one solver.
+struct Scalars {
+  double t, t_end, dt, alpha, cfl, min_ca;
+  double mean[4], area_total, dev[5];
+  long long steps, limited, nonphys, breaches;
+  int active, pad;
+};
+
+// ------------------------------------------------------------------------
+// Basis of eq. (basisfunc), modes 0..5, on the reference triangle
+// (v1 -> (0,0), v2 -> (1,0), v3 -> (0,1)).  Written as constexpr functions so
+// that evaluations at the fixed quadrature points fold to constants.
+// ------------------------------------------------------------------------
+__host__ __device__ constexpr double psi(int l, double x, double y) {
+  return l == 0 ? 1.0
+       : l == 1 ? 4.0 * x + 2.0 * y - 2.0
+       : l == 2 ? 3.0 * y - 1.0
+       : l == 3 ? 24.0 * x * x + 24.0 * x * y + 4.0 * y * y - 24.0 * x - 8.0 * y + 4.0
+       : l == 4 ? 20.0 * x * y + 10.0 * y * y - 4.0 * x - 12.0 * y + 2.0
+                : 10.0 * y * y - 8.0 * y + 1.0;
+}
+__host__ __device__ constexpr double psi_x(int l, double x, double y) {   // d/dxi
+  return l == 0 ? 0.0 : l == 1 ? 4.0 : l == 2 ? 0.0 : l == 3 ? 48.0 * x + 24.0 * y - 24.0
+       : l == 4 ? 20.0 * y - 4.0 : 0.0;
+}
+__host__ __device__ constexpr double psi_y(int l, double x, double y) {   // d/deta
+  return l == 0 ? 0.0 : l == 1 ? 2.0 : l == 2 ? 3.0 : l == 3 ? 24.0 * x + 8.0 * y - 8.0
+       : l == 4 ? 20.0 * x + 20.0 * y - 12.0 : 20.0 * y - 8.0;
+}
+// second reference derivatives: r = 0 (xi xi), 1 (xi eta), 2 (eta eta)
+__host__ __device__ constexpr double psi_2(int l, int r) {
+  return l == 3 ? (r == 0 ? 48.0 : r == 1 ? 24.0 : 8.0)
+       : l == 4 ? (r == 0 ? 0.0 : 20.0)
+       : l == 5 ? (r == 2 ? 20.0 : 0.0) : 0.0;
+}
+// mass a_K^(l) = c_l |K| of the orthogonal basis
+__host__ __device__ constexpr double mass_c(int l) {
+  return l == 0 ? 1.0 : l == 1 ? 2.0 / 3.0 : l == 2 ? 0.5 : l == 3 ? 16.0 / 15.0 : l == 4 ? 4.0 / 9.0 : 1.0 / 3.0;
+}
+__host__ __device__ constexpr int degree_of(int l) { return l == 0 ? 0 : (l <= 2 ? 1 : 2); }
+
+// Gauss-Legendre nodes of Appendix B mapped to s in (0, 1), weights summing to 1.
+__host__ __device__ constexpr double gauss_s(int Q, int nu) {
+  return Q == 2 ? (nu == 0 ? 0.21132486540518713 : 0.78867513459481287)
+                : (nu == 0 ? 0.11270166537925831 : nu == 1 ? 0.5 : 0.88729833462074169);
+}
+__host__ __device__ constexpr double gauss_w(int Q, int nu) {
+  return Q == 2 ? 0.5 : (nu == 1 ? 8.0 / 18.0 : 5.0 / 18.0);
+}
+// edge i is opposite vertex i, run from vertex i+1 to vertex i+2 (counter-clockwise)
+__host__ __device__ constexpr double edge_xi(int i, double s) { return i == 0 ? 1.0 - s : i == 1 ? 0.0 : s; }
+__host__ __device__ constexpr double edge_eta(int i, double s) { return i == 0 ? s : i == 1 ? 1.0 - s : 0.0; }
+__host__ __device__ constexpr double vert_xi(int v) { return v == 1 ? 1.0 : 0.0; }
+__host__ __device__ constexpr double vert_eta(int v) { return v == 2 ? 1.0 : 0.0; }
+
+// Volume rules of Appendix A (tab:2th for N = 3, tab:4th for N = 6); (xi, eta) = (b2, b3).
+__host__ __device__ constexpr double vol_xi(int N, int mu) {
+  return N == 3 ? (mu == 0 ? 1.0 / 6.0 : mu == 1 ? 2.0 / 3.0 : 1.0 / 6.0)
+       : (mu == 0 ? 0.445948490915965 : mu == 1 ? 0.108103018168070 : mu == 2 ? 0.445948490915965
+          : mu == 3 ? 0.091576213509771 : mu == 4 ? 0.816847572980458 : 0.091576213509771);
+}
+__host__ __device__ constexpr double vol_eta(int N, int mu) {
+  return N == 3 ? (mu == 0 ? 2.0 / 3.0 : mu == 1 ? 1.0 / 6.0 : 1.0 / 6.0)
+       : (mu == 0 ? 0.108103018168070 : mu == 1 ? 0.445948490915965 : mu == 2 ? 0.445948490915965
+          : mu == 3 ? 0.816847572980458 : mu == 4 ? 0.091576213509771 : 0.091576213509771);
+}
+__host__ __device__ constexpr double vol_w(int N, int mu) {
+  return N == 3 ? 1.0 / 3.0 : (mu < 3 ? 0.223381589678010 : 0.109951743655322);
+}
+
+// acc + c * x with a coefficient c known at compile time after unrolling:
+// zero terms vanish and unit coefficients become additions.
+template <typename T>
+__device__ __forceinline__ T cfma(double c, T x, T acc) {
+  if (c == 0.0) return acc;
+  if (c == 1.0) return acc + x;
+  if (c == -1.0) return acc - x;
+  return fma(static_cast<T>(c), x, acc);
+}
+
+// ------------------------------------------------------------------------
+// Euler physics (eq. euler, G:Euler)
+// ------------------------------------------------------------------------
+// F(u) . d for any direction d (not necessarily unit); returns pressure.
+template <typename T>
+__device__ __forceinline__ T flux_dir(const T u[4], T dx, T dy, T gm1, T f[4]) {
+  const T ri = T(1) / u[0];
+  const T p = gm1 * (u[3] - T(0.5) * (u[1] * u[1] + u[2] * u[2]) * ri);
+  const T md = u[1] * dx + u[2] * dy;
+  const T vd = md * ri;
+  f[0] = md;
+  f[1] = fma(u[1], vd, p * dx);
+  f[2] = fma(u[2], vd, p * dy);
+  f[3] = (u[3] + p) * vd;
+  return p;
+}
+
+// spectral radius |v.n| + c; +inf for rho <= 0, pressure clamped at 0
+template <typename T>
+__device__ __forceinline__ T wave_speed(const T u[4], T nx, T ny, T gamma) {
+  if (!(u[0] > T(0))) return T(INFINITY);
+  const T ri = T(1) / u[0];
+  T p = (gamma - T(1)) * (u[3] - T(0.5) * (u[1] * u[1] + u[2] * u[2]) * ri);
+  p = p > T(0) ? p : T(0);
+  return fabs(u[1] * nx + u[2] * ny) * ri + sqrt(gamma * p * ri);
+}
+
+__device__ __forceinline__ double int_energy(const double u[4]) {
+  return u[3] - 0.5 * (u[1] * u[1] + u[2] * u[2]) / u[0];
+}
+
+// exterior state of a boundary edge (tag > 0) at physical point (px, py), time t
+template <typename T>
+__device__ __forceinline__ void ghost_state(int tag, const T um[4], T nx, T ny, double px, double py, double t,
+                                            const Phys &ph, T up[4]) {
+  if (tag == 1) {                       // reflecting wall
+    const T mn = um[1] * nx + um[2] * ny;
+    up[0] = um[0];
+    up[1] = um[1] - T(2) * mn * nx;
+    up[2] = um[2] - T(2) * mn * ny;
+    up[3] = um[3];
+  } else if (tag >= 3 && tag <= 6) {    // constant state
+#pragma unroll
+    for (int c = 0; c < 4; ++c) up[c] = T(ph.bc[tag - 3][c]);
+  } else if (tag == 7) {                // moving shock
+    const double xs = ph.shock_x0 + py * ph.shock_cot + t * ph.shock_vx;
+    const int s = px < xs ? ph.shock_post : ph.shock_pre;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) up[c] = T(ph.bc[s][c]);
+  } else {                              // transmissive
+#pragma unroll
+    for (int c = 0; c < 4; ++c) up[c] = um[c];
+  }
+}
+
+// ------------------------------------------------------------------------
+// Deterministic block reductions (fixed shuffle tree, then warps in order)
+// ------------------------------------------------------------------------
+template <int N, typename T, typename Op>
+__device__ __forceinline__ void block_reduce(T v[N], T *out, Op op) {
+  __shared__ T red[TPB / 32][N > 0 ? N : 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < N; ++q) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[q] = op(v[q], __shfl_down_sync(0xffffffffu, v[q], o));
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < N; ++q) red[warp][q] = v[q];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+      T s = red[0][q];
+      for (int w = 1; w < TPB / 32; ++w) s = op(s, red[w][q]);
+      out[q] = s;
+    }
+  }
+}
+
+struct OpSum { template <typename T> __device__ T operator()(T a, T b) const { return a + b; } };
+struct OpMax {
+  __device__ double operator()(double a, double b) const { return (a > b || a != a) ? a : b; }
+};
+
+}  // namespace dg

@@ -1,0 +1,46 @@
+// dg_internal.h -- host-side interface between the C ABI (dg_api.cu) and the
+// kernel launch wrappers (dg_kernels.cu).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "dg_common.cuh"
+
+namespace dg {
+
+struct GeomPtrs {
+  double *area, *jinv, *nrm, *len, *node, *c_area;
+  int8_t *limv;
+};
+
+// a modal state: FP64 averages [4][nt] + higher modes [4][nb-1][nt] (double or float)
+struct StateBuf {
+  double *avg;
+  void *hi;
+};
+
+// everything a stage launch needs
+struct StageCtx {
+  cudaStream_t stream;
+  int k, prec;
+  MeshDev mesh;
+  Phys phys;
+  void *tr, *vd, *hs;
+  double *part_sum, *part_dev, *part_alpha;
+  long long *part_cnt;
+  Scalars *sc;
+};
+
+void launch_geometry(cudaStream_t s, int64_t nt, const double *vxy, const GeomPtrs &g, double *part_min,
+                     double *out_min4);
+void launch_rk(const StageCtx &c, const StateBuf &v, const StateBuf &un, const StateBuf &uh, double a, double b,
+               double c_in);
+void launch_fin_mean(const StageCtx &c);
+void launch_stats(const StageCtx &c, const StateBuf &uh);
+void launch_oe_bp(const StageCtx &c, const StateBuf &uh, const StateBuf &out, int do_oe, int do_bp, double c_out,
+                  int stage);
+void launch_step_begin(const StageCtx &c);
+void launch_set_active(const StageCtx &c, int active);
+int64_t num_blocks(int64_t nt);
+
+}  // namespace dg

@@ -1,0 +1,570 @@
+// dg_stage.cuh -- the per-stage kernels of the SSP-RK3 BP RI-OEDG scheme
+// (Ding, Cui & Wu, arXiv 2409.09620, Sec. 4.5), one thread per cell.
+//
+//   k_rk      volume quadrature + edge LF fluxes + mass inverse + RK combine
+//             (eqs. DGSystem:Dis, fluxLF, RKTime); publishes the vertex
+//             derivatives of u_h and block sums of |K| u_h^(0)
+//   k_stats   sup deviations from the domain mean at the volume points
+//             (eqs. normOmg, RIOESys:Coef1)
+//   k_oe_bp   RIOE damping (eqs. oe:sys, OEScalar:Coef1/Coef2, oe:sysdelta2,
+//             RIOESys:CoefM) + BP limiter (Sec. 4.4) + traces, F.n and the
+//             maximum wave speed of the limited state at the edge Gauss points
+//             (eq. 1250) for the next stage
+#pragma once
+#include "dg_common.cuh"
+
+namespace dg {
+
+template <typename Real, int NB>
+__device__ __forceinline__ void load_state(const StateDev<Real> &s, int64_t nt, int64_t K, double avg[4],
+                                           Real hi[4][NB]) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    avg[c] = s.avg[c * nt + K];
+    hi[c][0] = Real(0);
+#pragma unroll
+    for (int l = 1; l < NB; ++l) hi[c][l] = s.hi[(c * (NB - 1) + (l - 1)) * nt + K];
+  }
+}
+
+// value of the cell polynomial at a fixed reference point (compile-time after unrolling)
+template <typename Real, int NB>
+__device__ __forceinline__ void eval_fixed(const double avg[4], const Real hi[4][NB], double xi, double eta,
+                                           Real out[4]) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    Real s = Real(avg[c]);
+#pragma unroll
+    for (int l = 1; l < NB; ++l) s = cfma(psi(l, xi, eta), hi[c][l], s);
+    out[c] = s;
+  }
+}
+
+// ==========================================================================
+// K1: u_h = a u_n + b (v + dt L(v))
+// ==========================================================================
+template <int K, typename Real>
+__global__ void __launch_bounds__(TPB) k_rk(MeshDev m, Phys ph, StateDev<Real> v, StateDev<Real> un,
+                                            StateDev<Real> uh, const Real *__restrict__ tr,
+                                            Real *__restrict__ vdo, Real *__restrict__ hso,
+                                            double *__restrict__ part_sum, const Scalars *__restrict__ sc,
+                                            double a, double b, double c_in) {
+  constexpr int NB = Deg<K>::NB, NQ = Deg<K>::NQ, NV = Deg<K>::NV;
+  if (!sc->active) return;
+  const int64_t nt = m.nt;
+  const int64_t Kc = (int64_t)blockIdx.x * TPB + threadIdx.x;
+  double mass[4] = {0.0, 0.0, 0.0, 0.0};
+  if (Kc < nt) {
+    const double dt = sc->dt, alpha_d = sc->alpha, t_in = sc->t + c_in * sc->dt;
+    const Real alpha = Real(alpha_d), gm1 = Real(ph.gamma - 1.0);
+    const double area = m.area[Kc];
+    const Real jx = Real(m.jinv[Kc]), jy = Real(m.jinv[nt + Kc]);
+    const Real ex = Real(m.jinv[2 * nt + Kc]), ey = Real(m.jinv[3 * nt + Kc]);
+    double v0[4];
+    Real cv[4][NB];
+    load_state<Real, NB>(v, nt, Kc, v0, cv);
+
+    // ---- volume term: |K| sum_mu w_mu F(u(x_mu)) . grad Psi_l ---------------
+    Real acc[4][NB];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int l = 0; l < NB; ++l) acc[c][l] = Real(0);
+#pragma unroll
+    for (int mu = 0; mu < NV; ++mu) {
+      const double xi = vol_xi(NV, mu), eta = vol_eta(NV, mu), w = vol_w(NV, mu);
+      Real u[4], g1[4], g2[4];
+      eval_fixed<Real, NB>(v0, cv, xi, eta, u);
+      // F . grad Psi = (F . grad xi) dPsi/dxi + (F . grad eta) dPsi/deta
+      flux_dir(u, jx, jy, gm1, g1);
+      flux_dir(u, ex, ey, gm1, g2);
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int l = 1; l < NB; ++l) {
+          acc[c][l] = cfma(w * psi_x(l, xi, eta), g1[c], acc[c][l]);
+          acc[c][l] = cfma(w * psi_y(l, xi, eta), g2[c], acc[c][l]);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int l = 1; l < NB; ++l) acc[c][l] *= Real(area);
+
+    // ---- edge term: - sum_i l_i sum_nu w_nu Fhat Psi_l -------------------------
+    double acc0[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int32_t cn = m.conn[i * nt + Kc];
+      const Real nx = Real(m.nrm[(2 * i) * nt + Kc]), ny = Real(m.nrm[(2 * i + 1) * nt + Kc]);
+      const Real li = Real(m.len[i * nt + Kc]);
+#pragma unroll
+      for (int nu = 0; nu < NQ; ++nu) {
+        const Real *own = tr + ((Kc * 3 + i) * NQ + nu) * 8;
+        Real um[4], fm[4], up[4], fp[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) { um[q] = own[q]; fm[q] = own[4 + q]; }
+        if (cn >= 0) {
+          const int64_t nb = cn >> 2;
+          const int j = cn & 3;
+          const Real *oth = tr + ((nb * 3 + j) * NQ + (NQ - 1 - nu)) * 8;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) { up[q] = oth[q]; fp[q] = -oth[4 + q]; }
+        } else {
+          double px = 0.0, py = 0.0;
+          if (cn == -7) {
+            const double s = gauss_s(NQ, nu);
+            const double xa = m.vxy[(2 * ((i + 1) % 3)) * nt + Kc], ya = m.vxy[(2 * ((i + 1) % 3) + 1) * nt + Kc];
+            const double xb = m.vxy[(2 * ((i + 2) % 3)) * nt + Kc], yb = m.vxy[(2 * ((i + 2) % 3) + 1) * nt + Kc];
+            px = xa + (xb - xa) * s;
+            py = ya + (yb - ya) * s;
+          }
+          ghost_state(-cn, um, nx, ny, px, py, t_in, ph, up);
+          if (cn == -2) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) fp[q] = fm[q];
+          } else {
+            flux_dir(up, nx, ny, gm1, fp);
+          }
+        }
+        const Real lw = li * Real(gauss_w(NQ, nu));
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const Real fh = Real(0.5) * (fm[c] + fp[c] - alpha * (up[c] - um[c]));
+          const Real tv = lw * fh;
+          acc0[c] -= double(tv);
+#pragma unroll
+          for (int l = 1; l < NB; ++l)
+            acc[c][l] = cfma(-psi(l, edge_xi(i, gauss_s(NQ, nu)), edge_eta(i, gauss_s(NQ, nu))), tv, acc[c][l]);
+        }
+      }
+    }
+
+    // ---- mass inverse and SSP-RK combination -----------------------------------
+    double un0[4];
+    Real cu[4][NB];
+    load_state<Real, NB>(un, nt, Kc, un0, cu);
+    const double dta = dt / area;
+    double h0[4];
+    Real hh[4][NB];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      h0[c] = a * un0[c] + b * (v0[c] + dta * acc0[c]);
+      uh.avg[c * nt + Kc] = h0[c];
+      mass[c] = area * h0[c];
+      hh[c][0] = Real(0);
+#pragma unroll
+      for (int l = 1; l < NB; ++l) {
+        const Real s = Real(dta / mass_c(l));
+        hh[c][l] = Real(a) * cu[c][l] + Real(b) * (cv[c][l] + s * acc[c][l]);
+        uh.hi[(c * (NB - 1) + (l - 1)) * nt + Kc] = hh[c][l];
+      }
+    }
+
+    // ---- vertex derivatives of u_h for the OE jumps ------------------------------
+    Real *vo = vdo + Kc * 36;
+#pragma unroll
+    for (int vv = 0; vv < 3; ++vv) {
+      const double xi = vert_xi(vv), eta = vert_eta(vv);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        Real val = Real(h0[c]), gx = Real(0), ge = Real(0);
+#pragma unroll
+        for (int l = 1; l < NB; ++l) {
+          val = cfma(psi(l, xi, eta), hh[c][l], val);
+          gx = cfma(psi_x(l, xi, eta), hh[c][l], gx);
+          ge = cfma(psi_y(l, xi, eta), hh[c][l], ge);
+        }
+        vo[vv * 12 + c] = val;
+        vo[vv * 12 + 4 + 2 * c] = gx * jx + ge * ex;
+        vo[vv * 12 + 5 + 2 * c] = gx * jy + ge * ey;
+      }
+    }
+    if (K == 2) {
+      Real *ho = hso + Kc * 12;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        Real hxx = Real(0), hxe = Real(0), hee = Real(0);
+#pragma unroll
+        for (int l = 3; l < NB; ++l) {
+          hxx = cfma(psi_2(l, 0), hh[c][l], hxx);
+          hxe = cfma(psi_2(l, 1), hh[c][l], hxe);
+          hee = cfma(psi_2(l, 2), hh[c][l], hee);
+        }
+        ho[3 * c + 0] = hxx * jx * jx + Real(2) * hxe * jx * ex + hee * ex * ex;
+        ho[3 * c + 1] = hxx * jx * jy + hxe * (jx * ey + jy * ex) + hee * ex * ey;
+        ho[3 * c + 2] = hxx * jy * jy + Real(2) * hxe * jy * ey + hee * ey * ey;
+      }
+    }
+  }
+  block_reduce<4>(mass, part_sum + 4 * blockIdx.x, OpSum());
+}
+
+// ==========================================================================
+// K2: sup deviations from the domain mean at the volume points
+// ==========================================================================
+template <int K, typename Real>
+__global__ void __launch_bounds__(TPB) k_stats(MeshDev m, StateDev<Real> uh, double *__restrict__ part_dev,
+                                               const Scalars *__restrict__ sc) {
+  constexpr int NB = Deg<K>::NB, NV = Deg<K>::NV;
+  if (!sc->active) return;
+  const int64_t nt = m.nt;
+  const int64_t Kc = (int64_t)blockIdx.x * TPB + threadIdx.x;
+  double d[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  if (Kc < nt) {
+    double a0[4];
+    Real hi[4][NB];
+    load_state<Real, NB>(uh, nt, Kc, a0, hi);
+    double off[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) off[c] = a0[c] - sc->mean[c];   // deviation of the cell mean
+#pragma unroll
+    for (int mu = 0; mu < NV; ++mu) {
+      Real u[4];
+      eval_fixed<Real, NB>(off, hi, vol_xi(NV, mu), vol_eta(NV, mu), u);
+      const double r = fabs(double(u[0])), e = fabs(double(u[3]));
+      const double mm = sqrt(double(u[1]) * double(u[1]) + double(u[2]) * double(u[2]));
+      d[0] = fmax(d[0], r);
+      d[1] = fmax(d[1], mm);
+      d[2] = fmax(d[2], e);
+      d[3] = fmax(d[3], fabs(double(u[1])));
+      d[4] = fmax(d[4], fabs(double(u[2])));
+    }
+  }
+  block_reduce<5>(d, part_dev + 5 * blockIdx.x, OpMax());
+}
+
+// ==========================================================================
+// K3: RIOE + BP limiter + traces / alpha of the limited state
+// ==========================================================================
+// exterior vertex data of a boundary edge: value, gradient (x, y) and Hessian (xx, xy, yy)
+template <typename Real>
+__device__ __forceinline__ void ghost_vertex(int tag, const Real val[4], const Real grd[8], const Real hes[12],
+                                             Real nx, Real ny, double px, double py, double t, const Phys &ph,
+                                             Real ov[4], Real og[8], Real oh[12]) {
+  if (tag == 1) {
+    // mirror polynomial: q(Rx) for rho, E and R m(Rx) for the momentum, R = I - 2 n n^T
+    const Real R00 = Real(1) - Real(2) * nx * nx, R01 = -Real(2) * nx * ny, R11 = Real(1) - Real(2) * ny * ny;
+    Real RHR[4][3];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const Real hxx = hes[3 * c], hxy = hes[3 * c + 1], hyy = hes[3 * c + 2];
+      // (R H R)_ab with R symmetric
+      const Real a0 = R00 * hxx + R01 * hxy, a1 = R00 * hxy + R01 * hyy;   // row 0 of R H
+      const Real b0 = R01 * hxx + R11 * hxy, b1 = R01 * hxy + R11 * hyy;   // row 1 of R H
+      RHR[c][0] = a0 * R00 + a1 * R01;
+      RHR[c][1] = a0 * R01 + a1 * R11;
+      RHR[c][2] = b0 * R01 + b1 * R11;
+    }
+#pragma unroll
+    for (int c = 0; c < 4; c += 3) {
+      ov[c] = val[c];
+      og[2 * c] = R00 * grd[2 * c] + R01 * grd[2 * c + 1];
+      og[2 * c + 1] = R01 * grd[2 * c] + R11 * grd[2 * c + 1];
+      oh[3 * c] = RHR[c][0]; oh[3 * c + 1] = RHR[c][1]; oh[3 * c + 2] = RHR[c][2];
+    }
+    ov[1] = R00 * val[1] + R01 * val[2];
+    ov[2] = R01 * val[1] + R11 * val[2];
+    // gradient matrix G[a][b] = d m_a / d x_b -> R G R
+    const Real G00 = grd[2], G01 = grd[3], G10 = grd[4], G11 = grd[5];
+    const Real A00 = R00 * G00 + R01 * G10, A01 = R00 * G01 + R01 * G11;
+    const Real A10 = R01 * G00 + R11 * G10, A11 = R01 * G01 + R11 * G11;
+    og[2] = A00 * R00 + A01 * R01; og[3] = A00 * R01 + A01 * R11;
+    og[4] = A10 * R00 + A11 * R01; og[5] = A10 * R01 + A11 * R11;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      oh[3 + r] = R00 * RHR[1][r] + R01 * RHR[2][r];
+      oh[6 + r] = R01 * RHR[1][r] + R11 * RHR[2][r];
+    }
+  } else if (tag >= 3) {   // constant exterior state: no derivatives
+    Real st[4];
+    ghost_state(tag, val, nx, ny, px, py, t, ph, st);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) ov[c] = st[c];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) og[q] = Real(0);
+#pragma unroll
+    for (int q = 0; q < 12; ++q) oh[q] = Real(0);
+  } else {                 // transmissive: the own polynomial
+#pragma unroll
+    for (int c = 0; c < 4; ++c) ov[c] = val[c];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) og[q] = grd[q];
+#pragma unroll
+    for (int q = 0; q < 12; ++q) oh[q] = hes[q];
+  }
+}
+
+template <int K, typename Real>
+__global__ void __launch_bounds__(TPB) k_oe_bp(MeshDev m, Phys ph, StateDev<Real> uh, StateDev<Real> out,
+                                               const Real *__restrict__ vdi, const Real *__restrict__ hsi,
+                                               Real *__restrict__ tr, double *__restrict__ part_alpha,
+                                               long long *__restrict__ part_cnt, const Scalars *__restrict__ sc,
+                                               int do_oe, int do_bp, double c_out) {
+  constexpr int NB = Deg<K>::NB, NQ = Deg<K>::NQ;
+  constexpr int NE = 3 * NQ;          // edge Gauss points
+  if (!sc->active) return;
+  const int64_t nt = m.nt;
+  const int64_t Kc = (int64_t)blockIdx.x * TPB + threadIdx.x;
+  double amax = 0.0;
+  long long cnt[2] = {0, 0};
+  if (Kc < nt) {
+    const double dt = sc->dt, t_out = sc->t + c_out * sc->dt;
+    const Real gamma = Real(ph.gamma);
+    double a0[4];
+    Real hi[4][NB];
+    load_state<Real, NB>(uh, nt, Kc, a0, hi);
+    const double area = m.area[Kc];
+    Real nxs[3], nys[3];
+    int32_t cns[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      nxs[i] = Real(m.nrm[(2 * i) * nt + Kc]);
+      nys[i] = Real(m.nrm[(2 * i + 1) * nt + Kc]);
+      cns[i] = m.conn[i * nt + Kc];
+    }
+
+    // ---------------------------- RIOE ---------------------------------------
+    if (do_oe) {
+      const double eps = 1e-12;
+      const int cw = ph.oe == 2;
+      const double mnorm = sqrt(sc->mean[1] * sc->mean[1] + sc->mean[2] * sc->mean[2]);
+      // normaliser per damped quantity q: rho, (m_n | m1), (m_t | m2), E; 0 = constant component
+      double Dq[4];
+      Dq[0] = sc->dev[0] <= eps * fmax(1.0, fabs(sc->mean[0])) ? 0.0 : sc->dev[0];
+      Dq[3] = sc->dev[2] <= eps * fmax(1.0, fabs(sc->mean[3])) ? 0.0 : sc->dev[2];
+      if (cw) {
+        Dq[1] = sc->dev[3] <= eps * fmax(1.0, fabs(sc->mean[1])) ? 0.0 : sc->dev[3];
+        Dq[2] = sc->dev[4] <= eps * fmax(1.0, fabs(sc->mean[2])) ? 0.0 : sc->dev[4];
+      } else {
+        Dq[1] = Dq[2] = sc->dev[1] <= eps * fmax(1.0, mnorm) ? 0.0 : sc->dev[1];
+      }
+      Real sig[4][K + 1];
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int j = 0; j <= K; ++j) sig[c][j] = Real(0);
+      const Real *vme = vdi + Kc * 36;
+      Real hme[12];
+#pragma unroll
+      for (int q = 0; q < 12; ++q) hme[q] = (K == 2) ? hsi[Kc * 12 + q] : Real(0);
+
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const Real nx = nxs[i], ny = nys[i];
+        const int32_t cn = cns[i];
+        const Real h = Real(2.0 * area / m.len[i * nt + Kc]);
+        Real Jq[4][K + 1];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int j = 0; j <= K; ++j) Jq[q][j] = Real(0);
+        Real beta = Real(0);
+        Real hot[12];
+        const Real *vnb = nullptr;
+        int jn = 0;
+        if (cn >= 0) {
+          vnb = vdi + (int64_t)(cn >> 2) * 36;
+          jn = cn & 3;
+          if (K == 2) {
+#pragma unroll
+            for (int q = 0; q < 12; ++q) hot[q] = hsi[(int64_t)(cn >> 2) * 12 + q];
+          }
+        }
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int ov = (i + 1 + e) % 3;                 // v_c then v_d
+          Real val[4], grd[8], xv[4], xg[8], xh[12];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) val[c] = vme[ov * 12 + c];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) grd[q] = vme[ov * 12 + 4 + q];
+          if (cn >= 0) {
+            const int xvtx = (jn + 2 - e) % 3;            // the neighbour's copy of this vertex
+#pragma unroll
+            for (int c = 0; c < 4; ++c) xv[c] = vnb[xvtx * 12 + c];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) xg[q] = vnb[xvtx * 12 + 4 + q];
+#pragma unroll
+            for (int q = 0; q < 12; ++q) xh[q] = K == 2 ? hot[q] : Real(0);
+          } else {
+            double px = 0.0, py = 0.0;
+            if (cn == -7) { px = m.vxy[(2 * ov) * nt + Kc]; py = m.vxy[(2 * ov + 1) * nt + Kc]; }
+            ghost_vertex(-cn, val, grd, hme, nx, ny, px, py, t_out, ph, xv, xg, xh);
+          }
+          beta = fmax(beta, wave_speed(val, nx, ny, gamma));
+          beta = fmax(beta, wave_speed(xv, nx, ny, gamma));
+          // jumps of (rho, m1, m2, E): value, gradient; Hessian at e == 0 only (constant)
+          Real jv[4], jg[4][2], jh[4][3];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            jv[c] = val[c] - xv[c];
+            jg[c][0] = grd[2 * c] - xg[2 * c];
+            jg[c][1] = grd[2 * c + 1] - xg[2 * c + 1];
+#pragma unroll
+            for (int r = 0; r < 3; ++r) jh[c][r] = hme[3 * c + r] - xh[3 * c + r];
+          }
+          if (!cw) {   // rotate the momentum jumps to (m_n, m_t) with K's normal
+            Real t0 = jv[1], t1 = jv[2];
+            jv[1] = t0 * nx + t1 * ny; jv[2] = -t0 * ny + t1 * nx;
+#pragma unroll
+            for (int d = 0; d < 2; ++d) {
+              t0 = jg[1][d]; t1 = jg[2][d];
+              jg[1][d] = t0 * nx + t1 * ny; jg[2][d] = -t0 * ny + t1 * nx;
+            }
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+              t0 = jh[1][r]; t1 = jh[2][r];
+              jh[1][r] = t0 * nx + t1 * ny; jh[2][r] = -t0 * ny + t1 * nx;
+            }
+          }
+          // trapezoidal rule: 1/2 sum_alpha C_j^alpha1 [d^alpha q]^2 at each endpoint
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            Jq[q][0] += Real(0.5) * jv[q] * jv[q];
+            Jq[q][1] += Real(0.5) * (jg[q][0] * jg[q][0] + jg[q][1] * jg[q][1]);
+            if (K == 2)
+              Jq[q][K] += Real(0.5) * (jh[q][0] * jh[q][0] + Real(2) * jh[q][1] * jh[q][1] + jh[q][2] * jh[q][2]);
+          }
+        }
+        // delta_q^j = A^{k,j} h^j sqrt(J) / D_q, A^{k,j} = (2j + 1) / ((2k - 1) j!)
+        const Real bh = beta / h;
+        Real hj = Real(1);
+#pragma unroll
+        for (int j = 0; j <= K; ++j) {
+          const double A = (2.0 * j + 1.0) / ((2.0 * K - 1.0) * (j == 2 ? 2.0 : 1.0));
+          Real dl[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            dl[q] = Dq[q] == 0.0 ? Real(0) : Real(A) * hj * sqrt(Jq[q][j]) / Real(Dq[q]);
+          if (!cw) { const Real dm = fmax(dl[1], dl[2]); dl[1] = dm; dl[2] = dm; }
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+            if (dl[c] != Real(0)) sig[c][j] += bh * dl[c];
+          hj *= h;
+        }
+      }
+      // exact solution of the damping ODE: mode of degree m times exp(-dt sum_{j<=m} sigma^j)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        Real s = sig[c][0];
+        Real fac[K + 1];
+#pragma unroll
+        for (int mdeg = 1; mdeg <= K; ++mdeg) {
+          s += sig[c][mdeg];
+          fac[mdeg] = exp(-Real(dt) * s);
+        }
+#pragma unroll
+        for (int l = 1; l < NB; ++l) hi[c][l] *= fac[degree_of(l)];
+      }
+    }
+
+    // ---------------------------- BP limiter ----------------------------------
+    // deviations u(x_p) - ubar at the edge Gauss points and the two extra points
+    double dev[NE + 2][4];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int nu = 0; nu < NQ; ++nu) {
+        const double xi = edge_xi(i, gauss_s(NQ, nu)), eta = edge_eta(i, gauss_s(NQ, nu));
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          double s = 0.0;
+#pragma unroll
+          for (int l = 1; l < NB; ++l) s = cfma(psi(l, xi, eta), double(hi[c][l]), s);
+          dev[i * NQ + nu][c] = s;
+        }
+      }
+    double th_r = 1.0, th_a = 1.0;
+    if (do_bp) {
+      double px[2], py[2];
+      if (K == 1) {
+        const int v1 = m.limv[Kc], v2 = m.limv[nt + Kc];
+        px[0] = vert_xi(v1); py[0] = vert_eta(v1); px[1] = vert_xi(v2); py[1] = vert_eta(v2);
+      } else {
+        px[0] = m.node[Kc]; py[0] = m.node[nt + Kc]; px[1] = m.node[2 * nt + Kc]; py[1] = m.node[3 * nt + Kc];
+      }
+#pragma unroll
+      for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          double s = 0.0;
+#pragma unroll
+          for (int l = 1; l < NB; ++l) s = fma(psi(l, px[p], py[p]), double(hi[c][l]), s);
+          dev[NE + p][c] = s;
+        }
+      const double Ebar = int_energy(a0);
+      if (!(a0[0] > 0.0) || !(Ebar > 0.0)) {
+        cnt[1] = 1;
+      } else {
+        // Step 1: density
+        double rmin = a0[0] + dev[0][0];
+#pragma unroll
+        for (int p = 1; p < NE + 2; ++p) rmin = fmin(rmin, a0[0] + dev[p][0]);
+        const double eps1 = fmin(a0[0], 1e-13);
+        double th1 = 1.0;
+        if (rmin < eps1) th1 = (a0[0] - eps1) / (a0[0] - rmin);
+        // Step 2: internal energy of the density-limited polynomial
+        double emin = INFINITY;
+#pragma unroll
+        for (int p = 0; p < NE + 2; ++p) {
+          const double w[4] = {a0[0] + th1 * dev[p][0], a0[1] + dev[p][1], a0[2] + dev[p][2], a0[3] + dev[p][3]};
+          emin = fmin(emin, int_energy(w));
+        }
+        const double eps2 = fmin(Ebar, 1e-13);
+        double th2 = 1.0;
+        if (emin < eps2) th2 = (Ebar - eps2) / (Ebar - emin);
+        th_r = th1 * th2;
+        th_a = th2;
+        if (th1 < 1.0 || th2 < 1.0) cnt[0] = 1;
+      }
+    }
+    // ---------------------------- output ----------------------------------------
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      out.avg[c * nt + Kc] = a0[c];
+      const double th = c == 0 ? th_r : th_a;
+#pragma unroll
+      for (int l = 1; l < NB; ++l) {
+        const Real val = th < 1.0 ? Real(th * double(hi[c][l])) : hi[c][l];
+        out.hi[(c * (NB - 1) + (l - 1)) * nt + Kc] = val;
+      }
+    }
+    // traces, F.n and wave speed of the limited state at the edge Gauss points
+    const Real gm1 = Real(ph.gamma - 1.0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+#pragma unroll
+      for (int nu = 0; nu < NQ; ++nu) {
+        Real u[4], f[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) u[c] = Real(a0[c] + (c == 0 ? th_r : th_a) * dev[i * NQ + nu][c]);
+        flux_dir(u, nxs[i], nys[i], gm1, f);
+        amax = OpMax()(amax, double(wave_speed(u, nxs[i], nys[i], gamma)));
+        Real *o = tr + ((Kc * 3 + i) * NQ + nu) * 8;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) { o[q] = u[q]; o[4 + q] = f[q]; }
+        if (cns[i] < 0 && cns[i] <= -3) {
+          double px = 0.0, py = 0.0;
+          if (cns[i] == -7) {
+            const double s = gauss_s(NQ, nu);
+            const double xa = m.vxy[(2 * ((i + 1) % 3)) * nt + Kc], ya = m.vxy[(2 * ((i + 1) % 3) + 1) * nt + Kc];
+            const double xb = m.vxy[(2 * ((i + 2) % 3)) * nt + Kc], yb = m.vxy[(2 * ((i + 2) % 3) + 1) * nt + Kc];
+            px = xa + (xb - xa) * s;
+            py = ya + (yb - ya) * s;
+          }
+          Real up[4];
+          ghost_state(-cns[i], u, nxs[i], nys[i], px, py, t_out, ph, up);
+          amax = OpMax()(amax, double(wave_speed(up, nxs[i], nys[i], gamma)));
+        }
+      }
+    }
+  }
+  double av[1] = {amax};
+  block_reduce<1>(av, part_alpha + blockIdx.x, OpMax());
+  __syncthreads();
+  long long cv[2] = {cnt[0], cnt[1]};
+  block_reduce<2>(cv, part_cnt + 2 * blockIdx.x, OpSum());
+}
+
+}  // namespace dg

@@ -1,0 +1,280 @@
+"""Thin ctypes binding of the C ABI in ``include/dg.h`` (argument marshalling
+only: every step of the solver runs in the CUDA library).
+
+Loading fails loudly when the library is missing or cannot be loaded: there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+DG_OK, DG_EINVAL, DG_EMESH, DG_ENOMEM, DG_ENONPHYS, DG_ECUDA, DG_ETIMEOUT, DG_EBUSY = 0, -1, -2, -3, -4, -5, -6, -7
+PREC_FP64, PREC_MIXED = 0, 1
+OE_OFF, OE_RI, OE_CW = 0, 1, 2
+BP_OFF, BP_ON = 0, 1
+DECOMP_OPTIMAL, DECOMP_ZXS = 0, 1
+
+_lib = None
+P = C.c_void_p
+i64, i32, dbl = C.c_int64, C.c_int32, C.c_double
+
+
+class DGError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"dg error {code}: {msg}")
+        self.code = code
+
+
+class Config(C.Structure):
+    _fields_ = [("k", i32), ("precision", i32), ("oe", i32), ("bp", i32), ("decomp", i32), ("reserved", i32),
+                ("gamma", dbl), ("cfl", dbl), ("bc_state", (dbl * 4) * 4), ("shock_x0", dbl),
+                ("shock_angle", dbl), ("shock_speed", dbl), ("shock_pre", i32), ("shock_post", i32)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("steps", i64), ("limited_cells", i64), ("nonphysical", i64), ("cfl_breaches", i64),
+                ("t", dbl), ("dt_last", dbl), ("alpha", dbl)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+# name -> (restype, argtypes); every symbol of include/dg.h
+SIGNATURES = {
+    "dg_mesh_create": (i32, [i64, P, i64, P, P, P, C.POINTER(P)]),
+    "dg_mesh_destroy": (None, [P]),
+    "dg_mesh_info": (i32, [P, i32, C.POINTER(i64), C.POINTER(dbl), C.POINTER(dbl)]),
+    "dg_mesh_neighbors": (i32, [P, P, P]),
+    "dg_mesh_geometry": (i32, [P, i32, i32, P, P, P, P, P, P]),
+    "dg_quad_points": (i32, [P, P]),
+    "dg_project": (i32, [P, i32, P, P]),
+    "dg_init": (i32, [P, C.POINTER(Config), P, P, C.POINTER(P)]),
+    "dg_advance": (i32, [P, dbl, i64, C.POINTER(Stats)]),
+    "dg_advance_async": (i32, [P, i64]),
+    "dg_sync": (i32, [P, C.POINTER(Stats)]),
+    "dg_get_state": (i32, [P, P, C.c_size_t, C.POINTER(dbl)]),
+    "dg_set_state": (i32, [P, P, dbl]),
+    "dg_stream": (P, [P]),
+    "dg_solver_destroy": (None, [P]),
+    "dg_op_rk_stage": (i32, [P, P, P, dbl, dbl, dbl, dbl, dbl, P]),
+    "dg_op_stats": (i32, [P, P, P]),
+    "dg_op_oe": (i32, [P, P, dbl, P, dbl, P]),
+    "dg_op_limit": (i32, [P, P, P, P]),
+    "dg_op_alpha": (i32, [P, P, dbl, C.POINTER(dbl)]),
+    "dg_last_error": (C.c_char_p, []),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = True):
+    """Load the CUDA library (building it if it is missing); raises if it cannot be loaded."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError(f"CUDA library {path} is missing; run build()")
+            _build.build()
+        L = C.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != DG_OK:
+        raise DGError(rc, lib().dg_last_error().decode())
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(P)
+
+
+def make_config(k, precision=PREC_FP64, oe=OE_RI, bp=BP_ON, decomp=DECOMP_OPTIMAL, gamma=1.4, cfl=1.0,
+                bc_state=None, shock=(0.0, 0.0, 0.0, 0, 0)):
+    cf = Config()
+    cf.k, cf.precision, cf.oe, cf.bp, cf.decomp, cf.reserved = k, precision, oe, bp, decomp, 0
+    cf.gamma, cf.cfl = gamma, cfl
+    if bc_state is not None:
+        for i in range(4):
+            for j in range(4):
+                cf.bc_state[i][j] = float(bc_state[i][j])
+    cf.shock_x0, cf.shock_angle, cf.shock_speed = float(shock[0]), float(shock[1]), float(shock[2])
+    cf.shock_pre, cf.shock_post = int(shock[3]), int(shock[4])
+    return cf
+
+
+def config_for(workload, **kw):
+    return make_config(workload.k, bc_state=workload.bc_state, shock=workload.shock, gamma=workload.gamma, **kw)
+
+
+class Mesh:
+    """dg_mesh handle built from host arrays."""
+
+    def __init__(self, xy, tri, canon=None, bc=None):
+        L = lib()
+        xy = np.ascontiguousarray(xy, dtype=np.float64)
+        tri = np.ascontiguousarray(tri, dtype=np.int32)
+        canon = None if canon is None else np.ascontiguousarray(canon, dtype=np.int32)
+        bc = None if bc is None else np.ascontiguousarray(bc, dtype=np.int8)
+        h = P()
+        _check(L.dg_mesh_create(xy.shape[0] if xy.ndim == 2 else xy.size // 2, _p(xy),
+                                tri.shape[0] if tri.ndim == 2 else tri.size // 3, _p(tri), _p(canon), _p(bc),
+                                C.byref(h)))
+        self.h = h
+        nt = i64()
+        L.dg_mesh_info(h, 0, C.byref(nt), None, None)
+        self.nt = int(nt.value)
+
+    @classmethod
+    def from_mesh(cls, m):
+        return cls(m.xy, m.tri, m.canon, m.bc)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().dg_mesh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def min_cfl_area(self, k, decomp=DECOMP_OPTIMAL):
+        p1, p2 = dbl(), dbl()
+        _check(lib().dg_mesh_info(self.h, decomp, None, C.byref(p1), C.byref(p2)))
+        return p1.value if k == 1 else p2.value
+
+    def neighbors(self):
+        nbr = np.empty((self.nt, 3), np.int32)
+        ne = np.empty((self.nt, 3), np.int32)
+        _check(lib().dg_mesh_neighbors(self.h, _p(nbr), _p(ne)))
+        return nbr, ne
+
+    def geometry(self, k, decomp=DECOMP_OPTIMAL):
+        nt = self.nt
+        out = dict(area=np.empty(nt), len=np.empty((nt, 3)), normal=np.empty((nt, 3, 2)), c_area=np.empty(nt),
+                   nodes=np.empty((nt, 2, 2)), limv=np.empty((nt, 2), np.int8))
+        _check(lib().dg_mesh_geometry(self.h, k, decomp, *[_p(out[n]) for n in
+                                                             ("area", "len", "normal", "c_area", "nodes", "limv")]))
+        return out
+
+    def quad_points(self):
+        xy = np.empty((self.nt, 12, 2))
+        _check(lib().dg_quad_points(self.h, _p(xy)))
+        return xy
+
+    def project(self, k, fn=None, cell_fn=None):
+        if cell_fn is not None:
+            vals = np.repeat(np.asarray(cell_fn(np.arange(self.nt)), np.float64)[:, None, :], 12, axis=1)
+        else:
+            xy = self.quad_points()
+            vals = np.asarray(fn(xy[..., 0], xy[..., 1]), np.float64)
+        vals = np.ascontiguousarray(vals.reshape(self.nt, 12, 4))
+        u = np.empty((4, 3 if k == 1 else 6, self.nt))
+        _check(lib().dg_project(self.h, k, _p(vals), _p(u)))
+        return u
+
+
+class Solver:
+    """dg_solver handle: state resident on the GPU."""
+
+    def __init__(self, mesh: Mesh, cfg: Config, coeffs, stream=None):
+        self.mesh = mesh
+        self.cfg = cfg
+        self.nb = 3 if cfg.k == 1 else 6
+        u = np.ascontiguousarray(coeffs, dtype=np.float64)
+        assert u.size == 4 * self.nb * mesh.nt
+        h = P()
+        st = None if stream is None else P(stream)
+        _check(lib().dg_init(mesh.h, C.byref(cfg), _p(u), st, C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().dg_solver_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def stream(self):
+        return lib().dg_stream(self.h)
+
+    def advance(self, t_end, max_steps=1 << 62, check=True):
+        st = Stats()
+        rc = lib().dg_advance(self.h, t_end, max_steps, C.byref(st))
+        if check:
+            _check(rc)
+        return st.as_dict() if not check else st.as_dict(), rc
+
+    def advance_async(self, n):
+        _check(lib().dg_advance_async(self.h, n))
+
+    def sync(self):
+        st = Stats()
+        _check(lib().dg_sync(self.h, C.byref(st)))
+        return st.as_dict()
+
+    def get_state(self):
+        u = np.empty((4, self.nb, self.mesh.nt))
+        t = dbl()
+        _check(lib().dg_get_state(self.h, _p(u), u.size, C.byref(t)))
+        return u, t.value
+
+    def set_state(self, u, t=0.0):
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        _check(lib().dg_set_state(self.h, _p(u), t))
+
+    # -- single operators (leave the solver state undefined) --------------------
+    def op_rk_stage(self, un, v, a, b, dt, alpha, t=0.0):
+        un = np.ascontiguousarray(un, np.float64); v = np.ascontiguousarray(v, np.float64)
+        out = np.empty_like(v)
+        _check(lib().dg_op_rk_stage(self.h, _p(un), _p(v), a, b, dt, alpha, t, _p(out)))
+        return out
+
+    def op_stats(self, u):
+        u = np.ascontiguousarray(u, np.float64)
+        st = np.empty(10)
+        _check(lib().dg_op_stats(self.h, _p(u), _p(st)))
+        return st
+
+    def op_oe(self, u, dt, stats, t=0.0):
+        u = np.ascontiguousarray(u, np.float64)
+        out = np.empty_like(u)
+        _check(lib().dg_op_oe(self.h, _p(u), dt, _p(np.ascontiguousarray(stats, np.float64)), t, _p(out)))
+        return out
+
+    def op_limit(self, u):
+        u = np.ascontiguousarray(u, np.float64)
+        out = np.empty_like(u)
+        cnt = np.zeros(2, np.int64)
+        _check(lib().dg_op_limit(self.h, _p(u), _p(out), _p(cnt)))
+        return out, cnt
+
+    def op_alpha(self, u, t=0.0):
+        u = np.ascontiguousarray(u, np.float64)
+        a = dbl()
+        _check(lib().dg_op_alpha(self.h, _p(u), t, C.byref(a)))
+        return a.value
+
+
+def initial_state(mesh: Mesh, workload):
+    """Projection of a workload's initial data with the library's own projection."""
+    return mesh.project(workload.k, fn=workload.u0, cell_fn=workload.cell_u0)

@@ -1,0 +1,262 @@
+"""GPU parity: each hot-path operator of the CUDA library, called through the
+C ABI, against the CPU oracle on the same seeded inputs.
+
+Tolerances: FP64 relative error <= 1e-12 after one operator / stage / step and
+<= 1e-9 after 100 steps, relative to the largest oracle magnitude of each
+conservative component.  Integer work (adjacency, limiter vertex ids,
+counters) is compared bit-exactly.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2409_09620_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL1 = 1e-12
+
+
+def rel_err(a, b):
+    scale = np.maximum(np.abs(b).reshape(4, -1).max(1), 1e-300)
+    return float((np.abs(a - b).reshape(4, -1).max(1) / scale).max())
+
+
+@pytest.fixture(scope="module")
+def N():
+    from paper_2409_09620_gb300 import native
+    native.lib()
+    return native
+
+
+def _dmr_small(k, nx=24, ny=8):
+    return W.dmr_workload(nx=nx, ny=ny, k=k)
+
+
+def _cases():
+    # (name, workload factory): periodic, reflecting, transmissive, Dirichlet + moving shock
+    return {
+        "vortex": lambda k: W.vortex_workload(n=13, k=k),          # 338 cells: 3 blocks, ragged tail
+        "sedov": lambda k: W.sedov_workload(n=14, k=k),
+        "riemann": lambda k: W.riemann4_workload(n=11, k=k),
+        "dmr": lambda k: _dmr_small(k),
+    }
+
+
+def _setup(oracle_mod, N, wl, precision=0, **kw):
+    O = oracle_mod
+    om = O.OracleMesh.from_mesh(wl.mesh)
+    u0 = O.project_workload(om, wl)
+    mesh = N.Mesh.from_mesh(wl.mesh)
+    cfg = N.config_for(wl, precision=precision, **kw)
+    solver = N.Solver(mesh, cfg, u0)
+    return om, u0, mesh, solver
+
+
+def _perturbed(u, seed, amp=0.02):
+    rng = np.random.default_rng(seed)
+    v = u.copy()
+    scale = np.abs(u[:, :1, :])
+    v[:, 1:, :] += amp * scale * rng.uniform(-1, 1, v[:, 1:, :].shape)
+    return v
+
+
+@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("case", ["vortex", "sedov", "dmr"])
+def test_geometry_and_adjacency(oracle_mod, N, k, case):
+    """Row a0: adjacency bit-exact; geometry and optimal decomposition vs the oracle."""
+    O = oracle_mod
+    wl = _cases()[case](k)
+    om = O.OracleMesh.from_mesh(wl.mesh)
+    mesh = N.Mesh.from_mesh(wl.mesh)
+    nb_o, ne_o = om.neighbors()
+    nb_g, ne_g = mesh.neighbors()
+    assert np.array_equal(nb_o, nb_g) and np.array_equal(ne_o, ne_g)
+    g = mesh.geometry(k)
+    area, ln, nrm = om.geometry()
+    np.testing.assert_allclose(g["area"], area, rtol=1e-14)
+    np.testing.assert_allclose(g["len"], ln, rtol=1e-14)
+    np.testing.assert_allclose(g["normal"], nrm, atol=1e-15)
+    V = wl.mesh.xy[wl.mesh.tri]
+    for K in range(0, wl.mesh.nt, 3):
+        d = om.decomposition(k, K)
+        np.testing.assert_allclose(g["c_area"][K], d["c_dcw"] * area[K], rtol=1e-13)
+        if k == 1:
+            assert list(g["limv"][K]) == list(d["limv"])
+        else:
+            for s in range(2):
+                xi, eta = g["nodes"][K, s]
+                p = V[K, 0] + xi * (V[K, 1] - V[K, 0]) + eta * (V[K, 2] - V[K, 0])
+                np.testing.assert_allclose(p, d["nodes"][s], atol=1e-14)
+    np.testing.assert_allclose(mesh.min_cfl_area(k), om.min_cfl_area(k, 0), rtol=1e-14)
+    np.testing.assert_allclose(mesh.min_cfl_area(k, 1), om.min_cfl_area(k, 1), rtol=1e-14)
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_projection(oracle_mod, N, k):
+    wl = W.vortex_workload(n=9, k=k)
+    om = oracle_mod.OracleMesh.from_mesh(wl.mesh)
+    mesh = N.Mesh.from_mesh(wl.mesh)
+    np.testing.assert_allclose(mesh.quad_points(), om.quad12_points(), atol=1e-15)
+    assert rel_err(mesh.project(k, fn=wl.u0), om.project(k, fn=wl.u0)) < 1e-13
+
+
+@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("case", ["vortex", "sedov", "riemann", "dmr"])
+def test_rk_stage(oracle_mod, N, k, case):
+    """Rows a1 + a2: volume quadrature, edge LF fluxes with neighbour traces or
+    boundary ghosts, mass inverse and the RK combination."""
+    O = oracle_mod
+    wl = _cases()[case](k)
+    om, u0, mesh, solver = _setup(O, N, wl)
+    cf = O.config_for(wl)
+    v = _perturbed(u0, 1)
+    un = _perturbed(u0, 2)
+    alpha = 1.3 * om.alpha(cf, v, 0.01)
+    dt = 0.5 * om.min_cfl_area(k) / alpha
+    for (a, b) in [(0.0, 1.0), (0.75, 0.25)]:
+        got = solver.op_rk_stage(un, v, a, b, dt, alpha, t=0.01)
+        exp = om.rk_stage(cf, un, v, a, b, dt, alpha, t=0.01)
+        assert rel_err(got, exp) < TOL1
+    # the spatial operator alone: L = (u_h - v) / dt at b = 1
+    got = solver.op_rk_stage(un, v, 0.0, 1.0, 1.0, alpha, t=0.01)
+    L = om.L(cf, v, alpha, t=0.01)
+    assert rel_err(got - v, L) < 1e-11
+
+
+@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("case", ["vortex", "sedov", "dmr"])
+def test_oe_stats_and_damping(oracle_mod, N, k, case):
+    """Rows a2b + a3: global OE statistics and the RIOE damping."""
+    O = oracle_mod
+    wl = _cases()[case](k)
+    om, u0, mesh, solver = _setup(O, N, wl)
+    cf = O.config_for(wl)
+    u = _perturbed(u0, 3, amp=0.05)
+    st_g = solver.op_stats(u)
+    st_o = om.stats(cf, u)
+    np.testing.assert_allclose(st_g[:4], st_o[:4], rtol=1e-13, atol=1e-15 * np.abs(st_o[:4]).max())
+    np.testing.assert_allclose(st_g[4:], st_o[4:], rtol=1e-12)
+    dt = 0.3 * om.min_cfl_area(k) / om.alpha(cf, u)
+    got = solver.op_oe(u, dt, st_o, t=0.02)
+    exp = om.oe(cf, u, dt, st_o, t=0.02)
+    assert np.array_equal(got[:, 0], u[:, 0])
+    assert rel_err(got, exp) < TOL1
+    assert np.abs(got - u).max() > 0    # damping happened
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_component_wise_oe(oracle_mod, N, k):
+    O = oracle_mod
+    wl = W.riemann4_workload(n=11, k=k)
+    om, u0, mesh, solver = _setup(O, N, wl, oe=2)
+    cf = O.config_for(wl, oe=2)
+    u = _perturbed(u0, 4, amp=0.05)
+    st = om.stats(cf, u)
+    got = solver.op_oe(u, 0.01, st)
+    assert rel_err(got, om.oe(cf, u, 0.01, st)) < TOL1
+
+
+@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("case", ["vortex", "sedov", "riemann"])
+def test_limiter(oracle_mod, N, k, case):
+    """Row a4: BP limiter at the optimal-decomposition points; counters exact."""
+    O = oracle_mod
+    wl = _cases()[case](k)
+    om, u0, mesh, solver = _setup(O, N, wl)
+    cf = O.config_for(wl)
+    u = _perturbed(u0, 5, amp=0.8 if k == 1 else 0.4)
+    got, cg = solver.op_limit(u)
+    exp, co = om.limit(cf, u)
+    assert np.array_equal(cg, co) and co[0] > 0
+    assert np.array_equal(got[:, 0], u[:, 0])
+    assert rel_err(got, exp) < TOL1
+
+
+@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("case", ["vortex", "sedov", "dmr"])
+def test_alpha(oracle_mod, N, k, case):
+    """Row a5: maximum wave speed at the edge Gauss points (ghosts included)."""
+    O = oracle_mod
+    wl = _cases()[case](k)
+    om, u0, mesh, solver = _setup(O, N, wl)
+    cf = O.config_for(wl)
+    u = _perturbed(u0, 6, amp=0.01)
+    for t in (0.0, 0.05):
+        np.testing.assert_allclose(solver.op_alpha(u, t), om.alpha(cf, u, t), rtol=1e-13)
+
+
+@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("case", ["vortex", "sedov", "riemann", "dmr"])
+def test_one_step(oracle_mod, N, k, case):
+    """All rows: one SSP-RK3 step of the graph-captured solver vs the oracle."""
+    O = oracle_mod
+    wl = _cases()[case](k)
+    om, u0, mesh, solver = _setup(O, N, wl)
+    cf = O.config_for(wl)
+    st, _ = solver.advance(10.0, max_steps=1)
+    ug, tg = solver.get_state()
+    uo, to, dto, cnt, rc = om.step(cf, u0, 0.0, 10.0)
+    assert rc == 0 and st["steps"] == 1
+    np.testing.assert_allclose(tg, to, rtol=1e-13)
+    assert rel_err(ug, uo) < TOL1
+    assert st["limited_cells"] == cnt[0] and st["cfl_breaches"] == cnt[2]
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_hundred_steps_vortex(oracle_mod, N, k):
+    """BP RI-OEDG on the isentropic vortex (32 x 32 jittered periodic grid, P1
+    is the small configuration of the benchmark family): 100 steps <= 1e-9."""
+    O = oracle_mod
+    wl = W.vortex_workload(n=32 if k == 1 else 16, k=k)
+    om, u0, mesh, solver = _setup(O, N, wl)
+    cf = O.config_for(wl)
+    solver.advance(10.0, max_steps=100)
+    ug, tg = solver.get_state()
+    uo, to, cnt, rc = om.advance(cf, u0, 0.0, 10.0, max_steps=100)
+    np.testing.assert_allclose(tg, to, rtol=1e-12)
+    assert rel_err(ug, uo) < 1e-9
+
+
+def test_advance_to_end_time(oracle_mod, N):
+    """dt clamped to t_end exactly; the whole config-1 run (vortex P1, t = 0.5)."""
+    O = oracle_mod
+    wl = W.vortex_workload(n=32, k=1)
+    om, u0, mesh, solver = _setup(O, N, wl)
+    st, _ = solver.advance(wl.t_end)
+    ug, tg = solver.get_state()
+    assert tg == wl.t_end
+    uo, to, cnt, rc = om.advance(O.config_for(wl), u0, 0.0, wl.t_end)
+    assert st["steps"] == cnt[3]
+    assert rel_err(ug, uo) < 1e-9
+
+
+def test_deterministic(oracle_mod, N):
+    wl = W.sedov_workload(n=20, k=2)
+    outs = []
+    for _ in range(2):
+        om, u0, mesh, solver = _setup(oracle_mod, N, wl)
+        solver.advance(10.0, max_steps=5)
+        outs.append(solver.get_state()[0])
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_errors(N):
+    xy = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]])
+    with pytest.raises(N.DGError) as e:
+        N.Mesh(xy, np.zeros((0, 3), np.int32))
+    assert e.value.code == N.DG_EINVAL
+    with pytest.raises(N.DGError) as e:
+        N.Mesh(xy, np.array([[0, 2, 1]], np.int32), None, np.ones((1, 3), np.int8))
+    assert e.value.code == N.DG_EMESH
+    mesh = N.Mesh(xy, np.array([[0, 1, 2]], np.int32), None, np.ones((1, 3), np.int8))
+    u = np.zeros((4, 3, 1))
+    u[0, 0] = -1.0
+    u[3, 0] = 1.0
+    with pytest.raises(N.DGError) as e:
+        N.Solver(mesh, N.make_config(1), u)
+    assert e.value.code == N.DG_ENONPHYS
+    with pytest.raises(N.DGError) as e:
+        N.Solver(mesh, N.make_config(3), np.zeros((4, 6, 1)))
+    assert e.value.code == N.DG_EINVAL
