@@ -154,6 +154,15 @@ int32_t dg_sync(dg_solver *solver, dg_stats *stats);
 int32_t dg_get_state(const dg_solver *solver, double *coeffs, size_t len, double *t);
 /* replace the state (host coefficients, used as given, not limited) and time */
 int32_t dg_set_state(dg_solver *solver, const double *coeffs, double t);
+/* Run n steps with the kernels of the captured step launched one by one and a
+ * CUDA event pair around each launch on the solver's stream (t_end is left as
+ * set by the last dg_advance call; use dg_advance_async-style open-ended runs
+ * for timing).  ms[q] and launches[q] receive the summed duration and launch
+ * count of kernel kind q: 0 step_begin (dt), 1 rk (volume + edge flux + RK
+ * combine), 2 fin_mean, 3 stats (OE normalisers), 4 fin_dev, 5 oe_bp (RIOE +
+ * limiter + traces), 6 fin_alpha. */
+#define DG_NUM_KERNEL_KINDS 7
+int32_t dg_profile_steps(dg_solver *solver, int64_t n, double *ms, int64_t *launches);
 /* the solver's CUDA stream (cudaStream_t) */
 void *dg_stream(const dg_solver *solver);
 void dg_solver_destroy(dg_solver *solver);

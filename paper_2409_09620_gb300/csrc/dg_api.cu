@@ -596,6 +596,50 @@ extern "C" int32_t dg_set_state(dg_solver *s, const double *coeffs, double t) {
   return DG_OK;
 }
 
+// Instrumented steps: the kernels of enqueue_step launched one by one with a
+// CUDA event pair around each launch, on the solver's stream.
+extern "C" int32_t dg_profile_steps(dg_solver *s, int64_t n, double *ms, int64_t *launches) {
+  if (!s || n < 0 || !ms || !launches) return fail(DG_EINVAL, "bad argument");
+  for (int q = 0; q < DG_NUM_KERNEL_KINDS; ++q) { ms[q] = 0.0; launches[q] = 0; }
+  const StageCtx &c = s->ctx;
+  const int oe = s->cfg.oe != DG_OE_OFF, bp = s->cfg.bp != DG_BP_OFF;
+  constexpr int MAXL = 1 + 3 * 6;
+  cudaEvent_t ev[2 * MAXL];
+  for (int i = 0; i < 2 * MAXL; ++i) CUDA_TRY(cudaEventCreate(&ev[i]));
+  int32_t rc = DG_OK;
+  for (int64_t step = 0; step < n && rc == DG_OK; ++step) {
+    int kind[MAXL], nl = 0;
+    auto rec = [&](int kd, auto &&fn) {
+      cudaEventRecord(ev[2 * nl], s->stream);
+      fn();
+      cudaEventRecord(ev[2 * nl + 1], s->stream);
+      kind[nl++] = kd;
+    };
+    rec(0, [&] { launch_step_begin(c); });
+    for (int st = 0; st < 3; ++st) {
+      const StateBuf &v = st == 0 ? s->un : s->us;
+      rec(1, [&] { launch_rk_only(c, v, s->un, s->uh, RK_A[st], RK_B[st], C_IN[st]); });
+      rec(2, [&] { launch_fin_mean(c); });
+      if (oe) {
+        rec(3, [&] { launch_stats_only(c, s->uh); });
+        rec(4, [&] { launch_fin_dev(c); });
+      }
+      rec(5, [&] { launch_oe_bp_only(c, s->uh, st == 2 ? s->un : s->us, oe, bp, C_OUT[st]); });
+      rec(6, [&] { launch_fin_alpha(c, st); });
+    }
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) { rc = fail(DG_ECUDA, "profiled step: %s", cudaGetErrorString(e)); break; }
+    for (int i = 0; i < nl; ++i) {
+      float t = 0.0f;
+      cudaEventElapsedTime(&t, ev[2 * i], ev[2 * i + 1]);
+      ms[kind[i]] += t;
+      launches[kind[i]] += 1;
+    }
+  }
+  for (int i = 0; i < 2 * MAXL; ++i) cudaEventDestroy(ev[i]);
+  return rc;
+}
+
 // ============================================================================
 // Single operators (host buffers).  They reuse the solver's buffers: the
 // solver state is undefined afterwards until dg_set_state.

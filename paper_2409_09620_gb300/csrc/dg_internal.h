@@ -36,6 +36,13 @@ void launch_geometry(cudaStream_t s, int64_t nt, const double *vxy, const GeomPt
 void launch_rk(const StageCtx &c, const StateBuf &v, const StateBuf &un, const StateBuf &uh, double a, double b,
                double c_in);
 void launch_fin_mean(const StageCtx &c);
+void launch_rk_only(const StageCtx &c, const StateBuf &v, const StateBuf &un, const StateBuf &uh, double a,
+                    double b, double c_in);
+void launch_stats_only(const StageCtx &c, const StateBuf &uh);
+void launch_fin_dev(const StageCtx &c);
+void launch_oe_bp_only(const StageCtx &c, const StateBuf &uh, const StateBuf &out, int do_oe, int do_bp,
+                       double c_out);
+void launch_fin_alpha(const StageCtx &c, int stage);
 void launch_stats(const StageCtx &c, const StateBuf &uh);
 void launch_oe_bp(const StageCtx &c, const StateBuf &uh, const StateBuf &out, int do_oe, int do_bp, double c_out,
                   int stage);

@@ -216,11 +216,16 @@ static void oebp_impl(cudaStream_t s, const MeshDev &m, const Phys &ph, StateDev
     }                                                        \
   } while (0)
 
-void launch_rk(const StageCtx &c, const StateBuf &v, const StateBuf &un, const StateBuf &uh, double a, double b,
-               double c_in) {
+void launch_rk_only(const StageCtx &c, const StateBuf &v, const StateBuf &un, const StateBuf &uh, double a,
+                    double b, double c_in) {
   DG_DISPATCH(c.k, c.prec,
               (rk_impl<KK, Real>(c.stream, c.mesh, c.phys, {v.avg, (Real *)v.hi}, {un.avg, (Real *)un.hi},
                                  {uh.avg, (Real *)uh.hi}, c.tr, c.vd, c.hs, c.part_sum, c.sc, a, b, c_in)));
+}
+
+void launch_rk(const StageCtx &c, const StateBuf &v, const StateBuf &un, const StateBuf &uh, double a, double b,
+               double c_in) {
+  launch_rk_only(c, v, un, uh, a, b, c_in);
   launch_fin_mean(c);
 }
 
@@ -228,17 +233,34 @@ void launch_fin_mean(const StageCtx &c) {
   k_fin_mean<<<1, FIN_THREADS, 0, c.stream>>>(c.part_sum, (int)nblocks(c.mesh.nt), c.sc);
 }
 
-void launch_stats(const StageCtx &c, const StateBuf &uh) {
+void launch_stats_only(const StageCtx &c, const StateBuf &uh) {
   DG_DISPATCH(c.k, c.prec, (stats_impl<KK, Real>(c.stream, c.mesh, {uh.avg, (Real *)uh.hi}, c.part_dev, c.sc)));
+}
+
+void launch_fin_dev(const StageCtx &c) {
   k_fin_dev<<<1, FIN_THREADS, 0, c.stream>>>(c.part_dev, (int)nblocks(c.mesh.nt), c.sc);
+}
+
+void launch_stats(const StageCtx &c, const StateBuf &uh) {
+  launch_stats_only(c, uh);
+  launch_fin_dev(c);
+}
+
+void launch_oe_bp_only(const StageCtx &c, const StateBuf &uh, const StateBuf &out, int do_oe, int do_bp,
+                       double c_out) {
+  DG_DISPATCH(c.k, c.prec,
+              (oebp_impl<KK, Real>(c.stream, c.mesh, c.phys, {uh.avg, (Real *)uh.hi}, {out.avg, (Real *)out.hi}, c.vd,
+                                   c.hs, c.tr, c.part_alpha, c.part_cnt, c.sc, do_oe, do_bp, c_out)));
+}
+
+void launch_fin_alpha(const StageCtx &c, int stage) {
+  k_fin_alpha<<<1, FIN_THREADS, 0, c.stream>>>(c.part_alpha, c.part_cnt, (int)nblocks(c.mesh.nt), c.sc, stage);
 }
 
 void launch_oe_bp(const StageCtx &c, const StateBuf &uh, const StateBuf &out, int do_oe, int do_bp, double c_out,
                   int stage) {
-  DG_DISPATCH(c.k, c.prec,
-              (oebp_impl<KK, Real>(c.stream, c.mesh, c.phys, {uh.avg, (Real *)uh.hi}, {out.avg, (Real *)out.hi}, c.vd,
-                                   c.hs, c.tr, c.part_alpha, c.part_cnt, c.sc, do_oe, do_bp, c_out)));
-  k_fin_alpha<<<1, FIN_THREADS, 0, c.stream>>>(c.part_alpha, c.part_cnt, (int)nblocks(c.mesh.nt), c.sc, stage);
+  launch_oe_bp_only(c, uh, out, do_oe, do_bp, c_out);
+  launch_fin_alpha(c, stage);
 }
 
 void launch_step_begin(const StageCtx &c) { k_step_begin<<<1, 32, 0, c.stream>>>(c.sc); }

@@ -66,6 +66,7 @@ SIGNATURES = {
     "dg_op_oe": (i32, [P, P, dbl, P, dbl, P]),
     "dg_op_limit": (i32, [P, P, P, P]),
     "dg_op_alpha": (i32, [P, P, dbl, C.POINTER(dbl)]),
+    "dg_profile_steps": (i32, [P, i64, P, P]),
     "dg_last_error": (C.c_char_p, []),
 }
 
@@ -241,6 +242,15 @@ class Solver:
     def set_state(self, u, t=0.0):
         u = np.ascontiguousarray(u, dtype=np.float64)
         _check(lib().dg_set_state(self.h, _p(u), t))
+
+    KERNEL_KINDS = ("step_begin", "rk", "fin_mean", "stats", "fin_dev", "oe_bp", "fin_alpha")
+
+    def profile_steps(self, n):
+        """n instrumented steps; per kernel kind: (summed ms, launches)."""
+        ms = np.zeros(7)
+        nl = np.zeros(7, np.int64)
+        _check(lib().dg_profile_steps(self.h, n, _p(ms), _p(nl)))
+        return {k: (float(ms[i]), int(nl[i])) for i, k in enumerate(self.KERNEL_KINDS)}
 
     # -- single operators (leave the solver state undefined) --------------------
     def op_rk_stage(self, un, v, a, b, dt, alpha, t=0.0):
