@@ -190,6 +190,31 @@ int32_t dg_op_limit(dg_solver *solver, const double *u, double *out, int64_t *co
 /* viscosity coefficient alpha of u at time t (eq. 1250) */
 int32_t dg_op_alpha(dg_solver *solver, const double *u, double t, double *alpha);
 
+/* ---------------------------------------------------------------------- */
+/* Statistics without device allocation                                    */
+/* ---------------------------------------------------------------------- */
+
+/* The OE global statistics of dg_op_stats (domain means and sup deviations at
+ * the volume points, stats[10] with the same layout) for callers that cannot
+ * allocate device memory when they call: hosts whose device memory is
+ * reserved by their own pool allocator, and loops that must not pay for an
+ * allocation or its implicit synchronisation.  The paper has no counterpart:
+ * this is an interface addition.
+ *
+ * coeffs is a DEVICE modal state [4][nb][nt] (layout above, nb from k) and
+ * stats a DEVICE array of 10 doubles, both owned by the caller; the work is
+ * enqueued on cuda_stream (a cudaStream_t, NULL = the legacy default stream)
+ * and the call returns without synchronising.  The call allocates nothing: its
+ * scratch is a fixed 2.36 MB device array inside the library, which every GPU
+ * that loads the library holds until exit.  The first call on a device looks up
+ * that array's device address (cudaGetSymbolAddress) with the device current,
+ * so make the first call on each device before any stream capture.  All calls
+ * on a device share the array and it keeps the last call's contents: calls
+ * whose kernels overlap on the same GPU race.  Errors: DG_EINVAL (NULL
+ * argument, k not 1 or 2, more than 4,194,304 cells), DG_ECUDA. */
+int32_t dg_stats_noalloc(const dg_mesh *mesh, int32_t k, const double *coeffs, double *stats,
+                         void *cuda_stream);
+
 /* thread-local message of the last error */
 const char *dg_last_error(void);
 

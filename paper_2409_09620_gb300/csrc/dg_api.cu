@@ -88,6 +88,15 @@ struct dg_solver {
 
 extern "C" const char *dg_last_error(void) { return g_err.c_str(); }
 
+namespace dg {
+void mesh_view(const dg_mesh *mesh, int64_t *nt, const double **area, double *area_total) {
+  *nt = mesh->nt;
+  *area = mesh->area;
+  *area_total = mesh->area_total;
+}
+int32_t set_error(int32_t code, const char *msg) { return fail(code, "%s", msg); }
+}  // namespace dg
+
 // ============================================================================
 // Mesh
 // ============================================================================

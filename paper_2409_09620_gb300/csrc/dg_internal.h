@@ -4,6 +4,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "../../include/dg.h"
 #include "dg_common.cuh"
 
 namespace dg {
@@ -49,5 +50,10 @@ void launch_oe_bp(const StageCtx &c, const StateBuf &uh, const StateBuf &out, in
 void launch_step_begin(const StageCtx &c);
 void launch_set_active(const StageCtx &c, int active);
 int64_t num_blocks(int64_t nt);
+
+// mesh size, device cell areas and their host-summed total (dg_api.cu)
+void mesh_view(const dg_mesh *mesh, int64_t *nt, const double **area, double *area_total);
+// record a message for dg_last_error and return code (dg_api.cu)
+int32_t set_error(int32_t code, const char *msg);
 
 }  // namespace dg

@@ -67,6 +67,7 @@ SIGNATURES = {
     "dg_op_limit": (i32, [P, P, P, P]),
     "dg_op_alpha": (i32, [P, P, dbl, C.POINTER(dbl)]),
     "dg_profile_steps": (i32, [P, i64, P, P]),
+    "dg_stats_noalloc": (i32, [P, i32, P, P, P]),
     "dg_last_error": (C.c_char_p, []),
 }
 
