@@ -52,14 +52,14 @@ struct dg_mesh {
   std::vector<double> vxy_host;         // [6][nt]
   // device
   double *area = nullptr, *jinv = nullptr, *nrm = nullptr, *len = nullptr, *vxy = nullptr, *node = nullptr,
-         *c_area = nullptr;
+         *c_area = nullptr, *hgeo = nullptr;
   int8_t *limv = nullptr;
   int32_t *conn = nullptr;
   double min_ca[4] = {0, 0, 0, 0};   // (P1 optimal, P1 ZXS, P2 optimal, P2 ZXS)
   double area_total = 0.0;
   ~dg_mesh() {
     cudaFree(area); cudaFree(jinv); cudaFree(nrm); cudaFree(len); cudaFree(vxy); cudaFree(node);
-    cudaFree(c_area); cudaFree(limv); cudaFree(conn);
+    cudaFree(c_area); cudaFree(limv); cudaFree(conn); cudaFree(hgeo);
   }
 };
 
@@ -193,6 +193,7 @@ extern "C" int32_t dg_mesh_create(int64_t nv, const double *xy, int64_t nt, cons
   MTRY(dalloc(&m->jinv, 4 * nt));
   MTRY(dalloc(&m->nrm, 6 * nt));
   MTRY(dalloc(&m->len, 3 * nt));
+  MTRY(dalloc(&m->hgeo, 6 * nt));
   MTRY(dalloc(&m->vxy, 6 * nt));
   MTRY(dalloc(&m->node, 4 * nt));
   MTRY(dalloc(&m->c_area, 4 * nt));
@@ -202,7 +203,7 @@ extern "C" int32_t dg_mesh_create(int64_t nv, const double *xy, int64_t nt, cons
   MTRY(dalloc(&mins, 4));
   MTRY(cudaMemcpy(m->vxy, m->vxy_host.data(), sizeof(double) * 6 * nt, cudaMemcpyHostToDevice));
   MTRY(cudaMemcpy(m->conn, conn.data(), sizeof(int32_t) * 3 * nt, cudaMemcpyHostToDevice));
-  GeomPtrs g{m->area, m->jinv, m->nrm, m->len, m->node, m->c_area, m->limv};
+  GeomPtrs g{m->area, m->jinv, m->nrm, m->len, m->hgeo, m->node, m->c_area, m->limv};
   launch_geometry(nullptr, nt, m->vxy, g, part, mins);
   MTRY(cudaGetLastError());
   MTRY(cudaMemcpy(m->min_ca, mins, sizeof(double) * 4, cudaMemcpyDeviceToHost));
@@ -445,7 +446,7 @@ extern "C" int32_t dg_init(const dg_mesh *mesh, const dg_config *cfg, const doub
   STRY(alloc_state(s, &s->uh));
   STRY(alloc_state(s, &s->us));
   STRY(cudaMalloc(&s->tr, rs * nt * 3 * nq * 8));
-  STRY(cudaMalloc(&s->vd, rs * nt * 36));
+  STRY(cudaMalloc(&s->vd, rs * nt * 42));
   STRY(cudaMalloc(&s->hs, rs * nt * 12));
   STRY(dalloc(&s->part_sum, 4 * nblk));
   STRY(dalloc(&s->part_dev, 5 * nblk));
@@ -457,7 +458,8 @@ extern "C" int32_t dg_init(const dg_mesh *mesh, const dg_config *cfg, const doub
   c.stream = s->stream;
   c.k = cfg->k;
   c.prec = cfg->precision;
-  c.mesh = MeshDev{nt, mesh->area, mesh->jinv, mesh->nrm, mesh->len, mesh->vxy, mesh->node, mesh->limv, mesh->conn};
+  c.mesh = MeshDev{nt,         mesh->area, mesh->jinv, mesh->nrm, mesh->len, mesh->vxy,
+                   mesh->node, mesh->hgeo, mesh->limv, mesh->conn};
   Phys &ph = c.phys;
   std::memset(&ph, 0, sizeof(ph));
   ph.gamma = cfg->gamma;
@@ -720,6 +722,7 @@ extern "C" int32_t dg_op_oe(dg_solver *s, const double *u, double dt, const doub
   h.t = t;
   h.dt = dt;
   if ((rc = write_scalars(s, &h)) != DG_OK) return rc;
+  launch_set_inv_normalisers(s->ctx);
   launch_oe_bp(s->ctx, s->uh, s->us, 1, 0, 0.0, -1);
   CUDA_TRY(cudaGetLastError());
   return download_state(s, s->us, out);

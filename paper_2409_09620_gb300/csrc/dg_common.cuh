@@ -4,11 +4,13 @@
 // Data layout in HBM (one mesh of nt cells):
 //   state     avg[4][nt] (FP64 cell averages, mode 0)  +  hi[4][nb-1][nt] (modes 1..nb-1, Real)
 //   geometry  area[nt], jinv[4][nt] (dxi/dx, dxi/dy, deta/dx, deta/dy), nrm[6][nt],
-//             len[3][nt], vxy[6][nt], node[4][nt] (P2 internal nodes, reference coords),
+//             len[3][nt], hgeo[6][nt] (h_i, 1/h_i), vxy[6][nt], node[4][nt] (P2 internal
+//             nodes, reference coords),
 //             limv[2][nt] (P1 limiter vertices), conn[3][nt] (neighbour << 2 | its edge, or -tag)
 //   exchange  tr[nt][3][Q][8]  traces of the stage input at edge Gauss points:
 //                              u (4) and F(u).n_i (4), written by the cell that owns them
-//             vd[nt][3][12]    value (4) and physical gradient (8) of u_h at each vertex
+//             vd[nt][3][14]    value (4), physical gradient (8), 1/rho and sound speed
+//                              of u_h at each vertex
 //             hs[nt][12]       physical Hessian (xx, xy, yy) of u_h per component (P2)
 // Every kernel is one thread per cell; reductions are per-block partials
 // reduced in a fixed order, so results are bitwise reproducible.
@@ -28,6 +30,7 @@ template <> struct Deg<2> { static constexpr int NB = 6, NQ = 3, NV = 6; };
 struct MeshDev {
   int64_t nt;
   const double *area, *jinv, *nrm, *len, *vxy, *node;
+  const double *hgeo;   // [6][nt]: h_i = 2|K| / l_i (i = 0..2), then 1 / h_i
   const int8_t *limv;
   const int32_t *conn;
 };
@@ -49,6 +52,7 @@ struct Phys {
 struct Scalars {
   double t, t_end, dt, alpha, cfl, min_ca;
   double mean[4], area_total, dev[5];
+  double invD[4];   // 1 / normaliser of the damped quantities (rho, m_n|m1, m_t|m2, E); 0 if constant
   long long steps, limited, nonphys, breaches;
   int active, pad;
 };
@@ -83,6 +87,10 @@ __host__ __device__ constexpr double psi_2(int l, int r) {
 // mass a_K^(l) = c_l |K| of the orthogonal basis
 __host__ __device__ constexpr double mass_c(int l) {
   return l == 0 ? 1.0 : l == 1 ? 2.0 / 3.0 : l == 2 ? 0.5 : l == 3 ? 16.0 / 15.0 : l == 4 ? 4.0 / 9.0 : 1.0 / 3.0;
+}
+// 1 / c_l (exact in binary)
+__host__ __device__ constexpr double inv_mass_c(int l) {
+  return l == 0 ? 1.0 : l == 1 ? 1.5 : l == 2 ? 2.0 : l == 3 ? 0.9375 : l == 4 ? 2.25 : 3.0;
 }
 __host__ __device__ constexpr int degree_of(int l) { return l == 0 ? 0 : (l <= 2 ? 1 : 2); }
 
@@ -140,6 +148,34 @@ __device__ __forceinline__ T flux_dir(const T u[4], T dx, T dy, T gm1, T f[4]) {
   f[2] = fma(u[2], vd, p * dy);
   f[3] = (u[3] + p) * vd;
   return p;
+}
+
+// F(u) . d1 and F(u) . d2 with one reciprocal of the density
+template <typename T>
+__device__ __forceinline__ void flux_dir2(const T u[4], T d1x, T d1y, T d2x, T d2y, T gm1, T f1[4], T f2[4]) {
+  const T ri = T(1) / u[0];
+  const T p = gm1 * (u[3] - T(0.5) * (u[1] * u[1] + u[2] * u[2]) * ri);
+  const T ep = u[3] + p;
+  const T m1 = u[1] * d1x + u[2] * d1y, v1 = m1 * ri;
+  const T m2 = u[1] * d2x + u[2] * d2y, v2 = m2 * ri;
+  f1[0] = m1; f1[1] = fma(u[1], v1, p * d1x); f1[2] = fma(u[2], v1, p * d1y); f1[3] = ep * v1;
+  f2[0] = m2; f2[1] = fma(u[1], v2, p * d2x); f2[2] = fma(u[2], v2, p * d2y); f2[3] = ep * v2;
+}
+
+// F(u) . n and the spectral radius |v.n| + c (+inf for rho <= 0) with one reciprocal
+template <typename T>
+__device__ __forceinline__ T flux_speed(const T u[4], T nx, T ny, T gm1, T gamma, T f[4]) {
+  const T ri = T(1) / u[0];
+  const T p = gm1 * (u[3] - T(0.5) * (u[1] * u[1] + u[2] * u[2]) * ri);
+  const T mn = u[1] * nx + u[2] * ny;
+  const T vn = mn * ri;
+  f[0] = mn;
+  f[1] = fma(u[1], vn, p * nx);
+  f[2] = fma(u[2], vn, p * ny);
+  f[3] = (u[3] + p) * vn;
+  if (!(u[0] > T(0))) return T(INFINITY);
+  const T pc = p > T(0) ? p : T(0);
+  return fabs(vn) + sqrt(gamma * pc * ri);
 }
 
 // spectral radius |v.n| + c; +inf for rho <= 0, pressure clamped at 0

@@ -10,7 +10,7 @@
 namespace dg {
 
 struct GeomPtrs {
-  double *area, *jinv, *nrm, *len, *node, *c_area;
+  double *area, *jinv, *nrm, *len, *hgeo, *node, *c_area;
   int8_t *limv;
 };
 
@@ -49,6 +49,7 @@ void launch_oe_bp(const StageCtx &c, const StateBuf &uh, const StateBuf &out, in
                   int stage);
 void launch_step_begin(const StageCtx &c);
 void launch_set_active(const StageCtx &c, int active);
+void launch_set_inv_normalisers(const StageCtx &c);
 int64_t num_blocks(int64_t nt);
 
 // mesh size, device cell areas and their host-summed total (dg_api.cu)

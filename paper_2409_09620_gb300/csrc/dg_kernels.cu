@@ -13,8 +13,8 @@ struct OpMinD { __device__ double operator()(double a, double b) const { return 
 // BP CFL numbers eqs. 1692, 1713; classical ZXS numbers of Sec. 4.3)
 // ==========================================================================
 __global__ void __launch_bounds__(TPB) k_geometry(int64_t nt, const double *__restrict__ vxy, double *area,
-                                                  double *jinv, double *nrm, double *len, double *node,
-                                                  int8_t *limv, double *c_area, double *part_min) {
+                                                  double *jinv, double *nrm, double *len, double *hgeo,
+                                                  double *node, int8_t *limv, double *c_area, double *part_min) {
   const int64_t K = (int64_t)blockIdx.x * TPB + threadIdx.x;
   double mins[4] = {INFINITY, INFINITY, INFINITY, INFINITY};
   if (K < nt) {
@@ -38,6 +38,9 @@ __global__ void __launch_bounds__(TPB) k_geometry(int64_t nt, const double *__re
       len[i * nt + K] = l[i];
       nrm[(2 * i) * nt + K] = dy / l[i];
       nrm[(2 * i + 1) * nt + K] = -dx / l[i];
+      // h_K^(i) = sup distance of K to edge i = the altitude 2|K| / l_i (OE coefficient, Sec. 2.3)
+      hgeo[i * nt + K] = 2.0 * ar / l[i];
+      hgeo[(3 + i) * nt + K] = l[i] / (2.0 * ar);
     }
     // relabel edges longest first (stable)
     int p0 = 0, p1 = 1, p2 = 2, tmp;
@@ -83,6 +86,22 @@ __global__ void __launch_bounds__(TPB) k_geometry(int64_t nt, const double *__re
   block_reduce<4>(mins, part_min + 4 * blockIdx.x, OpMinD());
 }
 
+// 1 / D_q of the damped quantities from sc->dev and sc->mean (eqs.
+// OEScalar:Coef2, RIOESys:Coef1/Coef2 with the round-off guard of Sec. 2.3)
+__device__ void write_inv_normalisers(Scalars *sc, int cw) {
+  const double eps = 1e-12;
+  auto inv = [&](double D, double ref) { return D <= eps * fmax(1.0, ref) ? 0.0 : 1.0 / D; };
+  sc->invD[0] = inv(sc->dev[0], fabs(sc->mean[0]));
+  sc->invD[3] = inv(sc->dev[2], fabs(sc->mean[3]));
+  if (cw) {
+    sc->invD[1] = inv(sc->dev[3], fabs(sc->mean[1]));
+    sc->invD[2] = inv(sc->dev[4], fabs(sc->mean[2]));
+  } else {
+    const double mnorm = sqrt(sc->mean[1] * sc->mean[1] + sc->mean[2] * sc->mean[2]);
+    sc->invD[1] = sc->invD[2] = inv(sc->dev[1], mnorm);
+  }
+}
+
 // ==========================================================================
 // Fixed-order reductions of block partials (one block)
 // ==========================================================================
@@ -123,12 +142,16 @@ __global__ void k_fin_mean(const double *part, int nblk, Scalars *sc) {
     for (int c = 0; c < 4; ++c) sc->mean[c] = r[c] / sc->area_total;
 }
 
-__global__ void k_fin_dev(const double *part, int nblk, Scalars *sc) {
+// sup deviations, then the reciprocal normalisers of the OE: a component whose
+// deviation is below 1e-12 max(1, |mean|) counts as constant (delta = 0)
+__global__ void k_fin_dev(const double *part, int nblk, Scalars *sc, int cw) {
   if (!sc->active) return;
   double r[5];
   fin_reduce<5>(part, nblk, 0.0, OpMax(), r);
-  if (threadIdx.x == 0)
+  if (threadIdx.x == 0) {
     for (int q = 0; q < 5; ++q) sc->dev[q] = r[q];
+    write_inv_normalisers(sc, cw);
+  }
 }
 
 // alpha of the new stage input and counters; after the last stage, t += dt
@@ -168,6 +191,10 @@ __global__ void k_step_begin(Scalars *sc) {
   }
 }
 
+__global__ void k_set_inv_normalisers(Scalars *sc, int cw) {
+  if (threadIdx.x == 0) write_inv_normalisers(sc, cw);
+}
+
 __global__ void k_set_active(Scalars *sc, int active) {
   if (threadIdx.x == 0) sc->active = active;
 }
@@ -180,7 +207,7 @@ static inline unsigned nblocks(int64_t nt) { return (unsigned)((nt + TPB - 1) / 
 void launch_geometry(cudaStream_t s, int64_t nt, const double *vxy, const GeomPtrs &g, double *part_min,
                      double *out_min4) {
   const unsigned nb = nblocks(nt);
-  k_geometry<<<nb, TPB, 0, s>>>(nt, vxy, g.area, g.jinv, g.nrm, g.len, g.node, g.limv, g.c_area, part_min);
+  k_geometry<<<nb, TPB, 0, s>>>(nt, vxy, g.area, g.jinv, g.nrm, g.len, g.hgeo, g.node, g.limv, g.c_area, part_min);
   k_fin_min4<<<1, FIN_THREADS, 0, s>>>(part_min, (int)nb, out_min4);
 }
 
@@ -238,7 +265,7 @@ void launch_stats_only(const StageCtx &c, const StateBuf &uh) {
 }
 
 void launch_fin_dev(const StageCtx &c) {
-  k_fin_dev<<<1, FIN_THREADS, 0, c.stream>>>(c.part_dev, (int)nblocks(c.mesh.nt), c.sc);
+  k_fin_dev<<<1, FIN_THREADS, 0, c.stream>>>(c.part_dev, (int)nblocks(c.mesh.nt), c.sc, c.phys.oe == 2);
 }
 
 void launch_stats(const StageCtx &c, const StateBuf &uh) {
@@ -265,6 +292,9 @@ void launch_oe_bp(const StageCtx &c, const StateBuf &uh, const StateBuf &out, in
 
 void launch_step_begin(const StageCtx &c) { k_step_begin<<<1, 32, 0, c.stream>>>(c.sc); }
 void launch_set_active(const StageCtx &c, int active) { k_set_active<<<1, 32, 0, c.stream>>>(c.sc, active); }
+void launch_set_inv_normalisers(const StageCtx &c) {
+  k_set_inv_normalisers<<<1, 32, 0, c.stream>>>(c.sc, c.phys.oe == 2);
+}
 
 int64_t num_blocks(int64_t nt) { return nblocks(nt); }
 

@@ -76,8 +76,7 @@ __global__ void __launch_bounds__(TPB) k_rk(MeshDev m, Phys ph, StateDev<Real> v
       Real u[4], g1[4], g2[4];
       eval_fixed<Real, NB>(v0, cv, xi, eta, u);
       // F . grad Psi = (F . grad xi) dPsi/dxi + (F . grad eta) dPsi/deta
-      flux_dir(u, jx, jy, gm1, g1);
-      flux_dir(u, ex, ey, gm1, g2);
+      flux_dir2(u, jx, jy, ex, ey, gm1, g1, g2);
 #pragma unroll
       for (int c = 0; c < 4; ++c)
 #pragma unroll
@@ -155,17 +154,19 @@ __global__ void __launch_bounds__(TPB) k_rk(MeshDev m, Phys ph, StateDev<Real> v
       hh[c][0] = Real(0);
 #pragma unroll
       for (int l = 1; l < NB; ++l) {
-        const Real s = Real(dta / mass_c(l));
+        const Real s = Real(dta * inv_mass_c(l));
         hh[c][l] = Real(a) * cu[c][l] + Real(b) * (cv[c][l] + s * acc[c][l]);
         uh.hi[(c * (NB - 1) + (l - 1)) * nt + Kc] = hh[c][l];
       }
     }
 
     // ---- vertex derivatives of u_h for the OE jumps ------------------------------
-    Real *vo = vdo + Kc * 36;
+    Real *vo = vdo + Kc * 42;
+    const Real gamma = Real(ph.gamma);
 #pragma unroll
     for (int vv = 0; vv < 3; ++vv) {
       const double xi = vert_xi(vv), eta = vert_eta(vv);
+      Real val4[4];
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         Real val = Real(h0[c]), gx = Real(0), ge = Real(0);
@@ -175,10 +176,21 @@ __global__ void __launch_bounds__(TPB) k_rk(MeshDev m, Phys ph, StateDev<Real> v
           gx = cfma(psi_x(l, xi, eta), hh[c][l], gx);
           ge = cfma(psi_y(l, xi, eta), hh[c][l], ge);
         }
-        vo[vv * 12 + c] = val;
-        vo[vv * 12 + 4 + 2 * c] = gx * jx + ge * ex;
-        vo[vv * 12 + 5 + 2 * c] = gx * jy + ge * ey;
+        val4[c] = val;
+        vo[vv * 14 + c] = val;
+        vo[vv * 14 + 4 + 2 * c] = gx * jx + ge * ex;
+        vo[vv * 14 + 5 + 2 * c] = gx * jy + ge * ey;
       }
+      // 1/rho and sound speed at the vertex, for the wave speeds beta of the OE (+inf for rho <= 0)
+      Real ri = Real(0), cs = Real(INFINITY);
+      if (val4[0] > Real(0)) {
+        ri = Real(1) / val4[0];
+        Real p = gm1 * (val4[3] - Real(0.5) * (val4[1] * val4[1] + val4[2] * val4[2]) * ri);
+        p = p > Real(0) ? p : Real(0);
+        cs = sqrt(gamma * p * ri);
+      }
+      vo[vv * 14 + 12] = ri;
+      vo[vv * 14 + 13] = cs;
     }
     if (K == 2) {
       Real *ho = hso + Kc * 12;
@@ -326,25 +338,17 @@ __global__ void __launch_bounds__(TPB) k_oe_bp(MeshDev m, Phys ph, StateDev<Real
 
     // ---------------------------- RIOE ---------------------------------------
     if (do_oe) {
-      const double eps = 1e-12;
       const int cw = ph.oe == 2;
-      const double mnorm = sqrt(sc->mean[1] * sc->mean[1] + sc->mean[2] * sc->mean[2]);
-      // normaliser per damped quantity q: rho, (m_n | m1), (m_t | m2), E; 0 = constant component
-      double Dq[4];
-      Dq[0] = sc->dev[0] <= eps * fmax(1.0, fabs(sc->mean[0])) ? 0.0 : sc->dev[0];
-      Dq[3] = sc->dev[2] <= eps * fmax(1.0, fabs(sc->mean[3])) ? 0.0 : sc->dev[2];
-      if (cw) {
-        Dq[1] = sc->dev[3] <= eps * fmax(1.0, fabs(sc->mean[1])) ? 0.0 : sc->dev[3];
-        Dq[2] = sc->dev[4] <= eps * fmax(1.0, fabs(sc->mean[2])) ? 0.0 : sc->dev[4];
-      } else {
-        Dq[1] = Dq[2] = sc->dev[1] <= eps * fmax(1.0, mnorm) ? 0.0 : sc->dev[1];
-      }
+      // 1 / normaliser of rho, (m_n | m1), (m_t | m2), E; 0 for a constant component
+      Real iD[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) iD[q] = Real(sc->invD[q]);
       Real sig[4][K + 1];
 #pragma unroll
       for (int c = 0; c < 4; ++c)
 #pragma unroll
         for (int j = 0; j <= K; ++j) sig[c][j] = Real(0);
-      const Real *vme = vdi + Kc * 36;
+      const Real *vme = vdi + Kc * 42;
       Real hme[12];
 #pragma unroll
       for (int q = 0; q < 12; ++q) hme[q] = (K == 2) ? hsi[Kc * 12 + q] : Real(0);
@@ -353,7 +357,7 @@ __global__ void __launch_bounds__(TPB) k_oe_bp(MeshDev m, Phys ph, StateDev<Real
       for (int i = 0; i < 3; ++i) {
         const Real nx = nxs[i], ny = nys[i];
         const int32_t cn = cns[i];
-        const Real h = Real(2.0 * area / m.len[i * nt + Kc]);
+        const Real h = Real(m.hgeo[i * nt + Kc]), ih = Real(m.hgeo[(3 + i) * nt + Kc]);
         Real Jq[4][K + 1];
 #pragma unroll
         for (int q = 0; q < 4; ++q)
@@ -364,7 +368,7 @@ __global__ void __launch_bounds__(TPB) k_oe_bp(MeshDev m, Phys ph, StateDev<Real
         const Real *vnb = nullptr;
         int jn = 0;
         if (cn >= 0) {
-          vnb = vdi + (int64_t)(cn >> 2) * 36;
+          vnb = vdi + (int64_t)(cn >> 2) * 42;
           jn = cn & 3;
           if (K == 2) {
 #pragma unroll
@@ -376,25 +380,30 @@ __global__ void __launch_bounds__(TPB) k_oe_bp(MeshDev m, Phys ph, StateDev<Real
           const int ov = (i + 1 + e) % 3;                 // v_c then v_d
           Real val[4], grd[8], xv[4], xg[8], xh[12];
 #pragma unroll
-          for (int c = 0; c < 4; ++c) val[c] = vme[ov * 12 + c];
+          for (int c = 0; c < 4; ++c) val[c] = vme[ov * 14 + c];
 #pragma unroll
-          for (int q = 0; q < 8; ++q) grd[q] = vme[ov * 12 + 4 + q];
+          for (int q = 0; q < 8; ++q) grd[q] = vme[ov * 14 + 4 + q];
+          // beta_K^(i): spectral radius |v.n| + c of both sides at both endpoints
+          const Real r_own = fabs(val[1] * nx + val[2] * ny) * vme[ov * 14 + 12] + vme[ov * 14 + 13];
+          Real r_oth;
           if (cn >= 0) {
             const int xvtx = (jn + 2 - e) % 3;            // the neighbour's copy of this vertex
 #pragma unroll
-            for (int c = 0; c < 4; ++c) xv[c] = vnb[xvtx * 12 + c];
+            for (int c = 0; c < 4; ++c) xv[c] = vnb[xvtx * 14 + c];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) xg[q] = vnb[xvtx * 12 + 4 + q];
+            for (int q = 0; q < 8; ++q) xg[q] = vnb[xvtx * 14 + 4 + q];
 #pragma unroll
             for (int q = 0; q < 12; ++q) xh[q] = K == 2 ? hot[q] : Real(0);
+            r_oth = fabs(xv[1] * nx + xv[2] * ny) * vnb[xvtx * 14 + 12] + vnb[xvtx * 14 + 13];
           } else {
             double px = 0.0, py = 0.0;
             if (cn == -7) { px = m.vxy[(2 * ov) * nt + Kc]; py = m.vxy[(2 * ov + 1) * nt + Kc]; }
             ghost_vertex(-cn, val, grd, hme, nx, ny, px, py, t_out, ph, xv, xg, xh);
+            // a mirror or copied state has the same spectral radius
+            r_oth = cn >= -2 ? r_own : wave_speed(xv, nx, ny, gamma);
           }
-          beta = fmax(beta, wave_speed(val, nx, ny, gamma));
-          beta = fmax(beta, wave_speed(xv, nx, ny, gamma));
-          // jumps of (rho, m1, m2, E): value, gradient; Hessian at e == 0 only (constant)
+          beta = fmax(beta, fmax(r_own, r_oth));
+          // jumps of (rho, m1, m2, E): value, gradient, Hessian
           Real jv[4], jg[4][2], jh[4][3];
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
@@ -427,17 +436,23 @@ __global__ void __launch_bounds__(TPB) k_oe_bp(MeshDev m, Phys ph, StateDev<Real
               Jq[q][K] += Real(0.5) * (jh[q][0] * jh[q][0] + Real(2) * jh[q][1] * jh[q][1] + jh[q][2] * jh[q][2]);
           }
         }
-        // delta_q^j = A^{k,j} h^j sqrt(J) / D_q, A^{k,j} = (2j + 1) / ((2k - 1) j!)
-        const Real bh = beta / h;
+        // delta_q^j = A^{k,j} h^j sqrt(J) / D_q, A^{k,j} = (2j + 1) / ((2k - 1) j!);
+        // RIOE: delta_m = max(delta_mn, delta_mt) = A h^j sqrt(max(J_mn, J_mt)) / D_m
+        const Real bh = beta * ih;
         Real hj = Real(1);
 #pragma unroll
         for (int j = 0; j <= K; ++j) {
-          const double A = (2.0 * j + 1.0) / ((2.0 * K - 1.0) * (j == 2 ? 2.0 : 1.0));
+          const Real Ah = Real((2.0 * j + 1.0) / ((2.0 * K - 1.0) * (j == 2 ? 2.0 : 1.0))) * hj;
           Real dl[4];
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-            dl[q] = Dq[q] == 0.0 ? Real(0) : Real(A) * hj * sqrt(Jq[q][j]) / Real(Dq[q]);
-          if (!cw) { const Real dm = fmax(dl[1], dl[2]); dl[1] = dm; dl[2] = dm; }
+          dl[0] = Ah * iD[0] * sqrt(Jq[0][j]);
+          dl[3] = Ah * iD[3] * sqrt(Jq[3][j]);
+          if (cw) {
+            dl[1] = Ah * iD[1] * sqrt(Jq[1][j]);
+            dl[2] = Ah * iD[2] * sqrt(Jq[2][j]);
+          } else {
+            dl[1] = Ah * iD[1] * sqrt(fmax(Jq[1][j], Jq[2][j]));
+            dl[2] = dl[1];
+          }
 #pragma unroll
           for (int c = 0; c < 4; ++c)
             if (dl[c] != Real(0)) sig[c][j] += bh * dl[c];
@@ -445,18 +460,25 @@ __global__ void __launch_bounds__(TPB) k_oe_bp(MeshDev m, Phys ph, StateDev<Real
         }
       }
       // exact solution of the damping ODE: mode of degree m times exp(-dt sum_{j<=m} sigma^j)
+      Real fac[4][K + 1];
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        Real s = sig[c][0];
-        Real fac[K + 1];
+        if (c == 2 && !cw) {   // RIOE: m2 shares the momentum coefficient of m1
 #pragma unroll
-        for (int mdeg = 1; mdeg <= K; ++mdeg) {
-          s += sig[c][mdeg];
-          fac[mdeg] = exp(-Real(dt) * s);
+          for (int md = 1; md <= K; ++md) fac[2][md] = fac[1][md];
+          continue;
         }
+        Real sacc = sig[c][0];
 #pragma unroll
-        for (int l = 1; l < NB; ++l) hi[c][l] *= fac[degree_of(l)];
+        for (int md = 1; md <= K; ++md) {
+          sacc += sig[c][md];
+          fac[c][md] = exp(-Real(dt) * sacc);
+        }
       }
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int l = 1; l < NB; ++l) hi[c][l] *= fac[c][degree_of(l)];
     }
 
     // ---------------------------- BP limiter ----------------------------------
@@ -505,13 +527,17 @@ __global__ void __launch_bounds__(TPB) k_oe_bp(MeshDev m, Phys ph, StateDev<Real
         double th1 = 1.0;
         if (rmin < eps1) th1 = (a0[0] - eps1) / (a0[0] - rmin);
         // Step 2: internal energy of the density-limited polynomial
+        // E - |m|^2 / (2 rho) < eps2 is tested as rho E - |m|^2 / 2 < eps2 rho (rho > 0):
+        // the division is only needed at points that violate the bound
+        const double eps2 = fmin(Ebar, 1e-13);
         double emin = INFINITY;
 #pragma unroll
         for (int p = 0; p < NE + 2; ++p) {
-          const double w[4] = {a0[0] + th1 * dev[p][0], a0[1] + dev[p][1], a0[2] + dev[p][2], a0[3] + dev[p][3]};
-          emin = fmin(emin, int_energy(w));
+          const double w0 = a0[0] + th1 * dev[p][0], w1 = a0[1] + dev[p][1], w2 = a0[2] + dev[p][2],
+                       w3 = a0[3] + dev[p][3];
+          const double q = 0.5 * (w1 * w1 + w2 * w2);
+          if (!(w0 > 0.0) || w3 * w0 - q < eps2 * w0) emin = fmin(emin, w3 - q / w0);
         }
-        const double eps2 = fmin(Ebar, 1e-13);
         double th2 = 1.0;
         if (emin < eps2) th2 = (Ebar - eps2) / (Ebar - emin);
         th_r = th1 * th2;
@@ -539,8 +565,7 @@ __global__ void __launch_bounds__(TPB) k_oe_bp(MeshDev m, Phys ph, StateDev<Real
         Real u[4], f[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) u[c] = Real(a0[c] + (c == 0 ? th_r : th_a) * dev[i * NQ + nu][c]);
-        flux_dir(u, nxs[i], nys[i], gm1, f);
-        amax = OpMax()(amax, double(wave_speed(u, nxs[i], nys[i], gamma)));
+        amax = OpMax()(amax, double(flux_speed(u, nxs[i], nys[i], gm1, gamma, f)));
         Real *o = tr + ((Kc * 3 + i) * NQ + nu) * 8;
 #pragma unroll
         for (int q = 0; q < 4; ++q) { o[q] = u[q]; o[4 + q] = f[q]; }
