@@ -324,6 +324,19 @@ def main():
                 tot2 = sum(v[0] for v in k2.values())
                 mixed["kernel_share"] = {k: round(v[0] / tot2, 4) for k, v in k2.items()}
             del s2
+            # density L1 difference from the FP64 path after the same number of steps
+            n_l1 = 20
+            sa = N.Solver(mesh, N.config_for(wl, precision=N.PREC_MIXED), u0)
+            sb = N.Solver(mesh, N.config_for(wl, precision=N.PREC_FP64), u0)
+            sa.advance(1e30, max_steps=n_l1)
+            sb.advance(1e30, max_steps=n_l1)
+            ua, _ = sa.get_state()
+            ub, _ = sb.get_state()
+            area = mesh.geometry(wl.k)["area"]
+            mixed["density_l1_rel_vs_fp64"] = float((np.abs(ua[0, 0] - ub[0, 0]) * area).sum()
+                                                    / (np.abs(ub[0, 0]) * area).sum())
+            mixed["density_l1_steps"] = n_l1
+            del sa, sb
         except Exception as exc:      # mixed precision not available
             mixed = {"error": str(exc)}
 

@@ -307,6 +307,231 @@ __device__ __forceinline__ void ghost_vertex(int tag, const Real val[4], const R
   }
 }
 
+// --------------------------------------------------------------------------
+// BP limiter and traces of the mixed-precision form (FP32 modes, FP64 cell
+// averages).  Every point of the limiter set is first screened in FP32 with a
+// margin far above the FP32 evaluation error; a cell that passes is admissible
+// with theta = 1.  Other cells get the paper's theta (Sec. 4.4) in FP64, with
+// the targets raised by the rounding that storing the scaled modes in FP32
+// can cause; the stored state is then re-evaluated in FP64 at every point and,
+// if a bound still fails, the cell falls back to its (admissible) average.
+// --------------------------------------------------------------------------
+template <int K>
+__device__ __forceinline__ void limit_and_trace_mixed(const MeshDev &m, const Phys &ph, const double a0[4],
+                                                      float hi[4][Deg<K>::NB], const float nxs[3],
+                                                      const float nys[3], const int32_t cns[3], StateDev<float> out,
+                                                      float *tr, int64_t Kc, double t_out, int do_bp, double &amax,
+                                                      long long cnt[2]) {
+  constexpr int NB = Deg<K>::NB, NQ = Deg<K>::NQ, NE = 3 * NQ;
+  const int64_t nt = m.nt;
+  const float gamma = float(ph.gamma), gm1 = float(ph.gamma - 1.0);
+  // the two extra points of the limiter set (P1: vertices v1, v2; P2: internal nodes)
+  double px[2], py[2];
+  if (K == 1) {
+    const int v1 = m.limv[Kc], v2 = m.limv[nt + Kc];
+    px[0] = vert_xi(v1); py[0] = vert_eta(v1); px[1] = vert_xi(v2); py[1] = vert_eta(v2);
+  } else {
+    px[0] = m.node[Kc]; py[0] = m.node[nt + Kc]; px[1] = m.node[2 * nt + Kc]; py[1] = m.node[3 * nt + Kc];
+  }
+  // FP32 deviations u - ubar at the edge Gauss points
+  float df[NE][4];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int nu = 0; nu < NQ; ++nu) {
+      const double xi = edge_xi(i, gauss_s(NQ, nu)), eta = edge_eta(i, gauss_s(NQ, nu));
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        float sacc = 0.0f;
+#pragma unroll
+        for (int l = 1; l < NB; ++l) sacc = cfma(psi(l, xi, eta), hi[c][l], sacc);
+        df[i * NQ + nu][c] = sacc;
+      }
+    }
+  bool lim64 = false;
+  if (do_bp) {
+    const double Ebar = int_energy(a0);
+    if (!(a0[0] > 0.0) || !(Ebar > 0.0)) {
+      cnt[1] = 1;
+    } else {
+      float S[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        S[c] = fabsf(float(a0[c]));
+#pragma unroll
+        for (int l = 1; l < NB; ++l) S[c] += 4.0f * fabsf(hi[c][l]);   // |Psi_l| <= 4 on K
+      }
+      const float eps1 = float(fmin(a0[0], 1e-13)), eps2 = float(fmin(Ebar, 1e-13));
+      auto passes = [&](const float d[4]) -> bool {
+        const float r = float(a0[0]) + d[0];
+        if (!(r >= eps1 + 1e-5f * S[0])) return false;
+        const float m1 = float(a0[1]) + d[1], m2 = float(a0[2]) + d[2], E = float(a0[3]) + d[3];
+        const float ri = 1.0f / r;
+        const float q = (m1 * m1 + m2 * m2) * ri;           // |m|^2 / rho
+        const float v = sqrtf(q * ri);                       // |v|
+        const float margin = 1e-5f * (S[3] + v * (S[1] + S[2]) + v * v * S[0]) + 1e-6f * (fabsf(E) + q);
+        return E - 0.5f * q >= eps2 + margin;
+      };
+      bool ok = true;
+#pragma unroll
+      for (int p = 0; p < NE; ++p) ok = passes(df[p]) && ok;
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        float d[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          float sacc = 0.0f;
+#pragma unroll
+          for (int l = 1; l < NB; ++l) sacc = fmaf(float(psi(l, px[p], py[p])), hi[c][l], sacc);
+          d[c] = sacc;
+        }
+        ok = passes(d) && ok;
+      }
+      lim64 = !ok;
+    }
+  }
+  float ut[NE][4];
+  if (!lim64) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      out.avg[c * nt + Kc] = a0[c];
+#pragma unroll
+      for (int l = 1; l < NB; ++l) out.hi[(c * (NB - 1) + (l - 1)) * nt + Kc] = hi[c][l];
+    }
+#pragma unroll
+    for (int p = 0; p < NE; ++p)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) ut[p][c] = float(a0[c]) + df[p][c];
+  } else {
+    // ---- FP64 theta (Sec. 4.4 Steps 1-2) with targets covering the FP32 store
+    double d[NE + 2][4], Sa[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      Sa[c] = 0.0;
+#pragma unroll
+      for (int l = 1; l < NB; ++l) Sa[c] += fabs(double(hi[c][l]));
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int nu = 0; nu < NQ; ++nu) {
+        const double xi = edge_xi(i, gauss_s(NQ, nu)), eta = edge_eta(i, gauss_s(NQ, nu));
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          double sacc = 0.0;
+#pragma unroll
+          for (int l = 1; l < NB; ++l) sacc = cfma(psi(l, xi, eta), double(hi[c][l]), sacc);
+          d[i * NQ + nu][c] = sacc;
+        }
+      }
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        double sacc = 0.0;
+#pragma unroll
+        for (int l = 1; l < NB; ++l) sacc = fma(psi(l, px[p], py[p]), double(hi[c][l]), sacc);
+        d[NE + p][c] = sacc;
+      }
+    const double r22 = 2.384185791015625e-07;   // 2^-22: |Psi| <= 4 times the FP32 half-ulp 2^-24
+    const double Ebar = int_energy(a0);
+    double rmin = INFINITY;
+#pragma unroll
+    for (int p = 0; p < NE + 2; ++p) rmin = fmin(rmin, a0[0] + d[p][0]);
+    const double eps1 = fmin(a0[0], 1e-13);
+    const double tgt1 = fmin(a0[0], eps1 + 2.0 * r22 * Sa[0]);
+    const double th1 = rmin < tgt1 ? (a0[0] - tgt1) / (a0[0] - rmin) : 1.0;
+    double emin = INFINITY, vmax2 = 0.0;
+#pragma unroll
+    for (int p = 0; p < NE + 2; ++p) {
+      const double w0 = a0[0] + th1 * d[p][0], w1 = a0[1] + d[p][1], w2 = a0[2] + d[p][2], w3 = a0[3] + d[p][3];
+      const double q = w1 * w1 + w2 * w2;
+      vmax2 = fmax(vmax2, q / (w0 * w0));
+      emin = fmin(emin, w3 - 0.5 * q / w0);
+    }
+    const double RE = r22 * (Sa[3] + sqrt(vmax2) * (Sa[1] + Sa[2]) + vmax2 * th1 * Sa[0]);
+    const double eps2 = fmin(Ebar, 1e-13);
+    const double tgt2 = fmin(Ebar, eps2 + 2.0 * RE);
+    const double th2 = emin < tgt2 ? (Ebar - tgt2) / (Ebar - emin) : 1.0;
+    float hs[4][NB];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      hs[c][0] = 0.0f;
+#pragma unroll
+      for (int l = 1; l < NB; ++l) hs[c][l] = float((c == 0 ? th1 * th2 : th2) * double(hi[c][l]));
+    }
+    // verify the stored FP32 modes in FP64 at every point of the set
+    bool bad = false;
+    double ud[NE][4];
+#pragma unroll
+    for (int p = 0; p < NE + 2; ++p) {
+      double w[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        double sacc = a0[c];
+        if (p < NE) {
+          const int i = p / NQ, nu = p % NQ;
+          const double xi = edge_xi(i, gauss_s(NQ, nu)), eta = edge_eta(i, gauss_s(NQ, nu));
+#pragma unroll
+          for (int l = 1; l < NB; ++l) sacc = cfma(psi(l, xi, eta), double(hs[c][l]), sacc);
+          ud[p][c] = sacc;
+        } else {
+#pragma unroll
+          for (int l = 1; l < NB; ++l) sacc = fma(psi(l, px[p - NE], py[p - NE]), double(hs[c][l]), sacc);
+        }
+        w[c] = sacc;
+      }
+      if (!(w[0] > 0.0) || !(int_energy(w) > 0.0)) bad = true;
+    }
+    if (bad) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+#pragma unroll
+        for (int l = 1; l < NB; ++l) hs[c][l] = 0.0f;
+#pragma unroll
+        for (int p = 0; p < NE; ++p) ud[p][c] = a0[c];
+      }
+    }
+    if (th1 < 1.0 || th2 < 1.0 || bad) cnt[0] = 1;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      out.avg[c * nt + Kc] = a0[c];
+#pragma unroll
+      for (int l = 1; l < NB; ++l) out.hi[(c * (NB - 1) + (l - 1)) * nt + Kc] = hs[c][l];
+    }
+#pragma unroll
+    for (int p = 0; p < NE; ++p)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) ut[p][c] = float(ud[p][c]);
+  }
+  // traces, F.n and wave speed at the edge Gauss points for the next stage
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+#pragma unroll
+    for (int nu = 0; nu < NQ; ++nu) {
+      float f[4];
+      const float *u = ut[i * NQ + nu];
+      amax = OpMax()(amax, double(flux_speed(u, nxs[i], nys[i], gm1, gamma, f)));
+      float *o = tr + ((Kc * 3 + i) * NQ + nu) * 8;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) { o[q] = u[q]; o[4 + q] = f[q]; }
+      if (cns[i] <= -3) {
+        double qx = 0.0, qy = 0.0;
+        if (cns[i] == -7) {
+          const double sg = gauss_s(NQ, nu);
+          const double xa = m.vxy[(2 * ((i + 1) % 3)) * nt + Kc], ya = m.vxy[(2 * ((i + 1) % 3) + 1) * nt + Kc];
+          const double xb = m.vxy[(2 * ((i + 2) % 3)) * nt + Kc], yb = m.vxy[(2 * ((i + 2) % 3) + 1) * nt + Kc];
+          qx = xa + (xb - xa) * sg;
+          qy = ya + (yb - ya) * sg;
+        }
+        float up[4];
+        ghost_state(-cns[i], u, nxs[i], nys[i], qx, qy, t_out, ph, up);
+        amax = OpMax()(amax, double(wave_speed(up, nxs[i], nys[i], gamma)));
+      }
+    }
+  }
+}
+
 template <int K, typename Real>
 __global__ void __launch_bounds__(TPB) k_oe_bp(MeshDev m, Phys ph, StateDev<Real> uh, StateDev<Real> out,
                                                const Real *__restrict__ vdi, const Real *__restrict__ hsi,
@@ -326,7 +551,6 @@ __global__ void __launch_bounds__(TPB) k_oe_bp(MeshDev m, Phys ph, StateDev<Real
     double a0[4];
     Real hi[4][NB];
     load_state<Real, NB>(uh, nt, Kc, a0, hi);
-    const double area = m.area[Kc];
     Real nxs[3], nys[3];
     int32_t cns[3];
 #pragma unroll
@@ -481,108 +705,112 @@ __global__ void __launch_bounds__(TPB) k_oe_bp(MeshDev m, Phys ph, StateDev<Real
         for (int l = 1; l < NB; ++l) hi[c][l] *= fac[c][degree_of(l)];
     }
 
-    // ---------------------------- BP limiter ----------------------------------
-    // deviations u(x_p) - ubar at the edge Gauss points and the two extra points
-    double dev[NE + 2][4];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int nu = 0; nu < NQ; ++nu) {
-        const double xi = edge_xi(i, gauss_s(NQ, nu)), eta = edge_eta(i, gauss_s(NQ, nu));
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          double s = 0.0;
-#pragma unroll
-          for (int l = 1; l < NB; ++l) s = cfma(psi(l, xi, eta), double(hi[c][l]), s);
-          dev[i * NQ + nu][c] = s;
-        }
-      }
-    double th_r = 1.0, th_a = 1.0;
-    if (do_bp) {
-      double px[2], py[2];
-      if (K == 1) {
-        const int v1 = m.limv[Kc], v2 = m.limv[nt + Kc];
-        px[0] = vert_xi(v1); py[0] = vert_eta(v1); px[1] = vert_xi(v2); py[1] = vert_eta(v2);
-      } else {
-        px[0] = m.node[Kc]; py[0] = m.node[nt + Kc]; px[1] = m.node[2 * nt + Kc]; py[1] = m.node[3 * nt + Kc];
-      }
-#pragma unroll
-      for (int p = 0; p < 2; ++p)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          double s = 0.0;
-#pragma unroll
-          for (int l = 1; l < NB; ++l) s = fma(psi(l, px[p], py[p]), double(hi[c][l]), s);
-          dev[NE + p][c] = s;
-        }
-      const double Ebar = int_energy(a0);
-      if (!(a0[0] > 0.0) || !(Ebar > 0.0)) {
-        cnt[1] = 1;
-      } else {
-        // Step 1: density
-        double rmin = a0[0] + dev[0][0];
-#pragma unroll
-        for (int p = 1; p < NE + 2; ++p) rmin = fmin(rmin, a0[0] + dev[p][0]);
-        const double eps1 = fmin(a0[0], 1e-13);
-        double th1 = 1.0;
-        if (rmin < eps1) th1 = (a0[0] - eps1) / (a0[0] - rmin);
-        // Step 2: internal energy of the density-limited polynomial
-        // E - |m|^2 / (2 rho) < eps2 is tested as rho E - |m|^2 / 2 < eps2 rho (rho > 0):
-        // the division is only needed at points that violate the bound
-        const double eps2 = fmin(Ebar, 1e-13);
-        double emin = INFINITY;
-#pragma unroll
-        for (int p = 0; p < NE + 2; ++p) {
-          const double w0 = a0[0] + th1 * dev[p][0], w1 = a0[1] + dev[p][1], w2 = a0[2] + dev[p][2],
-                       w3 = a0[3] + dev[p][3];
-          const double q = 0.5 * (w1 * w1 + w2 * w2);
-          if (!(w0 > 0.0) || w3 * w0 - q < eps2 * w0) emin = fmin(emin, w3 - q / w0);
-        }
-        double th2 = 1.0;
-        if (emin < eps2) th2 = (Ebar - eps2) / (Ebar - emin);
-        th_r = th1 * th2;
-        th_a = th2;
-        if (th1 < 1.0 || th2 < 1.0) cnt[0] = 1;
-      }
-    }
-    // ---------------------------- output ----------------------------------------
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      out.avg[c * nt + Kc] = a0[c];
-      const double th = c == 0 ? th_r : th_a;
-#pragma unroll
-      for (int l = 1; l < NB; ++l) {
-        const Real val = th < 1.0 ? Real(th * double(hi[c][l])) : hi[c][l];
-        out.hi[(c * (NB - 1) + (l - 1)) * nt + Kc] = val;
-      }
-    }
-    // traces, F.n and wave speed of the limited state at the edge Gauss points
-    const Real gm1 = Real(ph.gamma - 1.0);
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-#pragma unroll
-      for (int nu = 0; nu < NQ; ++nu) {
-        Real u[4], f[4];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) u[c] = Real(a0[c] + (c == 0 ? th_r : th_a) * dev[i * NQ + nu][c]);
-        amax = OpMax()(amax, double(flux_speed(u, nxs[i], nys[i], gm1, gamma, f)));
-        Real *o = tr + ((Kc * 3 + i) * NQ + nu) * 8;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) { o[q] = u[q]; o[4 + q] = f[q]; }
-        if (cns[i] < 0 && cns[i] <= -3) {
-          double px = 0.0, py = 0.0;
-          if (cns[i] == -7) {
-            const double s = gauss_s(NQ, nu);
-            const double xa = m.vxy[(2 * ((i + 1) % 3)) * nt + Kc], ya = m.vxy[(2 * ((i + 1) % 3) + 1) * nt + Kc];
-            const double xb = m.vxy[(2 * ((i + 2) % 3)) * nt + Kc], yb = m.vxy[(2 * ((i + 2) % 3) + 1) * nt + Kc];
-            px = xa + (xb - xa) * s;
-            py = ya + (yb - ya) * s;
+    if constexpr (sizeof(Real) == sizeof(double)) {
+      // ---------------------------- BP limiter ----------------------------------
+      // deviations u(x_p) - ubar at the edge Gauss points and the two extra points
+      double dev[NE + 2][4];
+  #pragma unroll
+      for (int i = 0; i < 3; ++i)
+  #pragma unroll
+        for (int nu = 0; nu < NQ; ++nu) {
+          const double xi = edge_xi(i, gauss_s(NQ, nu)), eta = edge_eta(i, gauss_s(NQ, nu));
+  #pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            double s = 0.0;
+  #pragma unroll
+            for (int l = 1; l < NB; ++l) s = cfma(psi(l, xi, eta), double(hi[c][l]), s);
+            dev[i * NQ + nu][c] = s;
           }
-          Real up[4];
-          ghost_state(-cns[i], u, nxs[i], nys[i], px, py, t_out, ph, up);
-          amax = OpMax()(amax, double(wave_speed(up, nxs[i], nys[i], gamma)));
+        }
+      double th_r = 1.0, th_a = 1.0;
+      if (do_bp) {
+        double px[2], py[2];
+        if (K == 1) {
+          const int v1 = m.limv[Kc], v2 = m.limv[nt + Kc];
+          px[0] = vert_xi(v1); py[0] = vert_eta(v1); px[1] = vert_xi(v2); py[1] = vert_eta(v2);
+        } else {
+          px[0] = m.node[Kc]; py[0] = m.node[nt + Kc]; px[1] = m.node[2 * nt + Kc]; py[1] = m.node[3 * nt + Kc];
+        }
+  #pragma unroll
+        for (int p = 0; p < 2; ++p)
+  #pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            double s = 0.0;
+  #pragma unroll
+            for (int l = 1; l < NB; ++l) s = fma(psi(l, px[p], py[p]), double(hi[c][l]), s);
+            dev[NE + p][c] = s;
+          }
+        const double Ebar = int_energy(a0);
+        if (!(a0[0] > 0.0) || !(Ebar > 0.0)) {
+          cnt[1] = 1;
+        } else {
+          // Step 1: density
+          double rmin = a0[0] + dev[0][0];
+  #pragma unroll
+          for (int p = 1; p < NE + 2; ++p) rmin = fmin(rmin, a0[0] + dev[p][0]);
+          const double eps1 = fmin(a0[0], 1e-13);
+          double th1 = 1.0;
+          if (rmin < eps1) th1 = (a0[0] - eps1) / (a0[0] - rmin);
+          // Step 2: internal energy of the density-limited polynomial
+          // E - |m|^2 / (2 rho) < eps2 is tested as rho E - |m|^2 / 2 < eps2 rho (rho > 0):
+          // the division is only needed at points that violate the bound
+          const double eps2 = fmin(Ebar, 1e-13);
+          double emin = INFINITY;
+  #pragma unroll
+          for (int p = 0; p < NE + 2; ++p) {
+            const double w0 = a0[0] + th1 * dev[p][0], w1 = a0[1] + dev[p][1], w2 = a0[2] + dev[p][2],
+                         w3 = a0[3] + dev[p][3];
+            const double q = 0.5 * (w1 * w1 + w2 * w2);
+            if (!(w0 > 0.0) || w3 * w0 - q < eps2 * w0) emin = fmin(emin, w3 - q / w0);
+          }
+          double th2 = 1.0;
+          if (emin < eps2) th2 = (Ebar - eps2) / (Ebar - emin);
+          th_r = th1 * th2;
+          th_a = th2;
+          if (th1 < 1.0 || th2 < 1.0) cnt[0] = 1;
         }
       }
+      // ---------------------------- output ----------------------------------------
+  #pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        out.avg[c * nt + Kc] = a0[c];
+        const double th = c == 0 ? th_r : th_a;
+  #pragma unroll
+        for (int l = 1; l < NB; ++l) {
+          const Real val = th < 1.0 ? Real(th * double(hi[c][l])) : hi[c][l];
+          out.hi[(c * (NB - 1) + (l - 1)) * nt + Kc] = val;
+        }
+      }
+      // traces, F.n and wave speed of the limited state at the edge Gauss points
+      const Real gm1 = Real(ph.gamma - 1.0);
+  #pragma unroll
+      for (int i = 0; i < 3; ++i) {
+  #pragma unroll
+        for (int nu = 0; nu < NQ; ++nu) {
+          Real u[4], f[4];
+  #pragma unroll
+          for (int c = 0; c < 4; ++c) u[c] = Real(a0[c] + (c == 0 ? th_r : th_a) * dev[i * NQ + nu][c]);
+          amax = OpMax()(amax, double(flux_speed(u, nxs[i], nys[i], gm1, gamma, f)));
+          Real *o = tr + ((Kc * 3 + i) * NQ + nu) * 8;
+  #pragma unroll
+          for (int q = 0; q < 4; ++q) { o[q] = u[q]; o[4 + q] = f[q]; }
+          if (cns[i] < 0 && cns[i] <= -3) {
+            double px = 0.0, py = 0.0;
+            if (cns[i] == -7) {
+              const double s = gauss_s(NQ, nu);
+              const double xa = m.vxy[(2 * ((i + 1) % 3)) * nt + Kc], ya = m.vxy[(2 * ((i + 1) % 3) + 1) * nt + Kc];
+              const double xb = m.vxy[(2 * ((i + 2) % 3)) * nt + Kc], yb = m.vxy[(2 * ((i + 2) % 3) + 1) * nt + Kc];
+              px = xa + (xb - xa) * s;
+              py = ya + (yb - ya) * s;
+            }
+            Real up[4];
+            ghost_state(-cns[i], u, nxs[i], nys[i], px, py, t_out, ph, up);
+            amax = OpMax()(amax, double(wave_speed(up, nxs[i], nys[i], gamma)));
+          }
+        }
+      }
+    } else {
+      limit_and_trace_mixed<K>(m, ph, a0, hi, nxs, nys, cns, out, tr, Kc, t_out, do_bp, amax, cnt);
     }
   }
   double av[1] = {amax};
