@@ -222,6 +222,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=10)
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-steps", type=int, default=10)
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -340,6 +342,34 @@ def main():
         except Exception as exc:      # mixed precision not available
             mixed = {"error": str(exc)}
 
+    # batch of 64 independent solves, one persistent launch per RK stage
+    batch = None
+    if not args.no_batch:
+        from paper_2409_09620_gb300 import workloads as W
+        wls = W.batch_workloads(64)
+        bmeshes = [N.Mesh.from_mesh(w.mesh) for w in wls]
+        bus = [N.initial_state(m, w) for m, w in zip(bmeshes, wls)]
+        cells = sum(m.nt for m in bmeshes)
+        batch = {"solves": len(wls), "cells": cells, "p2_solves": sum(w.k == 2 for w in wls),
+                 "cells_min": min(m.nt for m in bmeshes), "cells_max": max(m.nt for m in bmeshes)}
+        for label, prec in (("fp64", N.PREC_FP64), ("fp32", N.PREC_MIXED)):
+            bt = N.Batch(bmeshes, [N.config_for(w, precision=prec) for w in wls], bus)
+            tune = bt.autotune(steps=2)
+            stream = torch.cuda.ExternalStream(bt.solver(0).stream)
+            bt.advance_async(args.warmup)
+            bt.sync()
+            barrier(world)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            bt.advance_async(args.batch_steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            bt.sync()
+            bms = dist_max(e0.elapsed_time(e1), world)
+            batch[label] = {"value": cells * 3 * args.batch_steps * world / (bms / 1e3),
+                            "ms_per_step": bms / args.batch_steps, "shape": bt.shape(), "autotune": tune}
+            del bt
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         wl_full = make_workload(args.workload, args.nx, args.ny)
@@ -357,7 +387,7 @@ def main():
                            "oe": "RI", "bp": "optimal-points", "cfl": 1.0,
                            "l2": "working set ~1.7 GB > 129 MB L2, no flush"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": 19 * args.steps, "clocks": clocks, "fp32": mixed,
+                "gpu_launches": 19 * args.steps, "clocks": clocks, "fp32": mixed, "batch": batch,
                 "peaks": {"source": peak_src, "hbm_gbs": peaks.get("hbm_gbs")},
                 "stats": {"limited_cells": st["limited_cells"], "cfl_breaches": st["cfl_breaches"],
                           "t": st["t"], "dt_last": st["dt_last"]}}

@@ -60,6 +60,7 @@ extern "C" {
 
 typedef struct dg_mesh dg_mesh;
 typedef struct dg_solver dg_solver;
+typedef struct dg_batch dg_batch;
 
 typedef struct dg_config {
   int32_t k;              /* polynomial degree: 1 or 2 */
@@ -189,6 +190,46 @@ int32_t dg_op_oe(dg_solver *solver, const double *u, double dt, const double *st
 int32_t dg_op_limit(dg_solver *solver, const double *u, double *out, int64_t *counters);
 /* viscosity coefficient alpha of u at time t (eq. 1250) */
 int32_t dg_op_alpha(dg_solver *solver, const double *u, double t, double *alpha);
+
+/* ---------------------------------------------------------------------- */
+/* Batches: many independent solves, one persistent launch per RK stage     */
+/* ---------------------------------------------------------------------- */
+
+/* Create a batch of n independent solves (meshes[i], cfgs[i], host initial
+ * coefficients coeffs[i]; k may differ between solves, the precision may not).
+ * Each solve is set up as by dg_init on the batch's stream (NULL = a stream
+ * the batch creates).  A time step of all solves is three cooperative
+ * launches of one persistent kernel (one per SSP-RK3 stage, captured as a CUDA
+ * graph when the runtime supports it); each launch walks a work list of
+ * (solve, cell range) chunks with grid barriers between the phases of the
+ * stage.  Every solve keeps its own alpha, dt, t and OE normalisers, and its
+ * results are bitwise those of the same solve run alone.  Errors as dg_init;
+ * DG_EINVAL if the precisions differ or the device lacks cooperative launch. */
+int32_t dg_batch_create(int32_t n, const dg_mesh *const *meshes, const dg_config *cfgs,
+                        const double *const *coeffs, void *cuda_stream, dg_batch **out);
+void dg_batch_destroy(dg_batch *batch);
+/* Advance every solve i until t_i >= t_end[i] (t_end NULL: +inf) or max_steps
+ * steps; solves that reached their end time idle.  stats (nullable) receives n
+ * entries.  A grid barrier that waits longer than 2 s ends the launch early
+ * and the call returns DG_ETIMEOUT. */
+int32_t dg_batch_advance(dg_batch *batch, const double *t_end, int64_t max_steps, dg_stats *stats);
+/* enqueue exactly n steps of every solve; pair with dg_batch_sync */
+int32_t dg_batch_advance_async(dg_batch *batch, int64_t nsteps);
+int32_t dg_batch_sync(dg_batch *batch);
+/* the solver handle of solve i (owned by the batch): dg_get_state /
+ * dg_set_state work on it; do not destroy it or advance it on its own */
+int32_t dg_batch_solver(dg_batch *batch, int32_t i, dg_solver **out);
+/* launch shape: cells per work chunk (a positive multiple of 128) and resident
+ * blocks per SM of the persistent grid (clamped to the occupancy limit) */
+int32_t dg_batch_set_shape(dg_batch *batch, int32_t cells_per_block, int32_t blocks_per_sm);
+int32_t dg_batch_shape(const dg_batch *batch, int32_t *cells_per_block, int32_t *blocks_per_sm,
+                       int32_t *grid, int32_t *graph);
+/* Time `steps` steps for every cells-per-chunk in {128, 256, 512, 1024} and
+ * every blocks-per-SM up to the occupancy limit, keep the fastest shape and
+ * restore every solve's state, time and counters.  The shape changes no
+ * result (partials are per 128 cells of each solve). */
+int32_t dg_batch_autotune(dg_batch *batch, int32_t steps, int32_t *best_cells_per_block,
+                          int32_t *best_blocks_per_sm, double *best_ms_per_step);
 
 /* ---------------------------------------------------------------------- */
 /* Statistics without device allocation                                    */

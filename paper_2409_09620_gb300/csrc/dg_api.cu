@@ -758,3 +758,18 @@ extern "C" int32_t dg_op_alpha(dg_solver *s, const double *u, double t, double *
   *alpha = r.alpha;
   return DG_OK;
 }
+
+// ============================================================================
+// Accessors used by the batch module
+// ============================================================================
+namespace dg {
+const StageCtx &solver_ctx(const dg_solver *s) { return s->ctx; }
+void solver_states(const dg_solver *s, StateBuf *un, StateBuf *uh, StateBuf *us) {
+  *un = s->un;
+  *uh = s->uh;
+  *us = s->us;
+}
+int solver_nb(const dg_solver *s) { return s->nb; }
+int32_t solver_read_scalars(const dg_solver *s, Scalars *h) { return read_scalars(s, h); }
+int32_t solver_write_scalars(dg_solver *s, const Scalars *h) { return write_scalars(s, h); }
+}  // namespace dg

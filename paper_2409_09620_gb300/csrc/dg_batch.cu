@@ -1,0 +1,475 @@
+// dg_batch.cu -- many independent solves advanced together: one persistent
+// (cooperative) launch per SSP-RK3 stage covers every solve.  Each launch runs
+// the phases of a stage (flux, means, OE normalisers, RIOE + limiter, alpha)
+// over a work list of (solve, tile range) chunks, separated by grid barriers.
+//
+// Every solve keeps its own buffers, scalars (t, dt, alpha, normalisers) and
+// per-tile partials; tiles never straddle solves and partials are per TPB
+// cells from each solve's first cell, so a solve's arithmetic does not depend
+// on the other solves or on the chunk size: results are bitwise those of the
+// same solve run alone.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "../../include/dg.h"
+#include "dg_internal.h"
+#include "dg_stage.cuh"
+
+namespace dg {
+
+struct SolveDev {
+  MeshDev mesh;
+  Phys ph;
+  double *avg[3];   // u_n, u_h, u_s
+  void *hi[3];
+  void *tr, *vd, *hs;
+  double *part_sum, *part_dev, *part_alpha;
+  long long *part_cnt;
+  Scalars *sc;
+  int k, oe, bp, pad;
+  int64_t ntiles;
+};
+
+struct WorkItem {
+  int solve;
+  int pad;
+  int64_t first_tile, ntiles;
+};
+
+struct BarrierState {
+  unsigned int count;
+  unsigned int gen;
+  int error;
+  int pad;
+};
+
+__constant__ double kRK_A[3] = {0.0, 0.75, 1.0 / 3.0};
+__constant__ double kRK_B[3] = {1.0, 0.25, 2.0 / 3.0};
+__constant__ double kC_IN[3] = {0.0, 1.0, 0.5};
+__constant__ double kC_OUT[3] = {1.0, 0.5, 1.0};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier for a cooperative launch (all blocks resident).  The wait
+// is bounded: after 2 s the block records an error and leaves; every block
+// then returns false and the kernel ends early (the host reports DG_ETIMEOUT).
+__device__ __forceinline__ bool grid_sync(BarrierState *b, unsigned nblocks) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned *vgen = &b->gen;
+    const unsigned g = *vgen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&b->count, 1u);
+    if (arrived == nblocks - 1) {
+      atomicExch(&b->count, 0u);
+      __threadfence();
+      atomicAdd(&b->gen, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (*vgen == g) {
+        if (global_ns() - t0 > 2000000000ull) {
+          atomicExch(&b->error, 1);
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+    s_ok = *(volatile int *)&b->error == 0;
+  }
+  __syncthreads();
+  return s_ok;
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(TPB) k_batch_stage(const SolveDev *__restrict__ sv, int nsv,
+                                                     const WorkItem *__restrict__ work, int nwork,
+                                                     BarrierState *bar, int stage) {
+  const unsigned nb = gridDim.x;
+  const double a = kRK_A[stage], b = kRK_B[stage], c_in = kC_IN[stage], c_out = kC_OUT[stage];
+  const int vi = stage == 0 ? 0 : 2;     // stage input: u_n, then u_s
+  const int oi = stage == 2 ? 0 : 2;     // stage output: u_s, last stage writes u_n
+  if (stage == 0) {
+    if (threadIdx.x == 0)
+      for (int i = blockIdx.x; i < nsv; i += gridDim.x) step_begin_thread(sv[i].sc);
+    if (!grid_sync(bar, nb)) return;
+  }
+  // phase 1: volume + edge fluxes + RK combination
+  for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+    const WorkItem it = work[w];
+    const SolveDev &S = sv[it.solve];
+    if (!S.sc->active) continue;
+    const StateDev<Real> v{S.avg[vi], (Real *)S.hi[vi]}, un{S.avg[0], (Real *)S.hi[0]}, uh{S.avg[1], (Real *)S.hi[1]};
+    for (int64_t t = it.first_tile; t < it.first_tile + it.ntiles; ++t) {
+      if (S.k == 1)
+        rk_tile<1, Real>(S.mesh, S.ph, v, un, uh, (const Real *)S.tr, (Real *)S.vd, (Real *)S.hs, S.part_sum, S.sc,
+                         a, b, c_in, t);
+      else
+        rk_tile<2, Real>(S.mesh, S.ph, v, un, uh, (const Real *)S.tr, (Real *)S.vd, (Real *)S.hs, S.part_sum, S.sc,
+                         a, b, c_in, t);
+    }
+  }
+  if (!grid_sync(bar, nb)) return;
+  // phase 2: domain means
+  for (int i = blockIdx.x; i < nsv; i += gridDim.x)
+    if (sv[i].sc->active) fin_mean_block(sv[i].part_sum, (int)sv[i].ntiles, sv[i].sc);
+  if (!grid_sync(bar, nb)) return;
+  // phase 3: sup deviations at the volume points (OE normalisers)
+  for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+    const WorkItem it = work[w];
+    const SolveDev &S = sv[it.solve];
+    if (!S.sc->active || !S.oe) continue;
+    const StateDev<Real> uh{S.avg[1], (Real *)S.hi[1]};
+    for (int64_t t = it.first_tile; t < it.first_tile + it.ntiles; ++t) {
+      if (S.k == 1) stats_tile<1, Real>(S.mesh, uh, S.part_dev, S.sc, t);
+      else stats_tile<2, Real>(S.mesh, uh, S.part_dev, S.sc, t);
+    }
+  }
+  if (!grid_sync(bar, nb)) return;
+  for (int i = blockIdx.x; i < nsv; i += gridDim.x)
+    if (sv[i].sc->active && sv[i].oe) fin_dev_block(sv[i].part_dev, (int)sv[i].ntiles, sv[i].sc, sv[i].oe == 2);
+  if (!grid_sync(bar, nb)) return;
+  // phase 5: RIOE + BP limiter + traces and alpha of the stage result
+  for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+    const WorkItem it = work[w];
+    const SolveDev &S = sv[it.solve];
+    if (!S.sc->active) continue;
+    const StateDev<Real> uh{S.avg[1], (Real *)S.hi[1]}, out{S.avg[oi], (Real *)S.hi[oi]};
+    for (int64_t t = it.first_tile; t < it.first_tile + it.ntiles; ++t) {
+      if (S.k == 1)
+        oe_bp_tile<1, Real>(S.mesh, S.ph, uh, out, (const Real *)S.vd, (const Real *)S.hs, (Real *)S.tr,
+                            S.part_alpha, S.part_cnt, S.sc, S.oe != 0, S.bp != 0, c_out, t);
+      else
+        oe_bp_tile<2, Real>(S.mesh, S.ph, uh, out, (const Real *)S.vd, (const Real *)S.hs, (Real *)S.tr,
+                            S.part_alpha, S.part_cnt, S.sc, S.oe != 0, S.bp != 0, c_out, t);
+    }
+  }
+  if (!grid_sync(bar, nb)) return;
+  // phase 6: alpha of the next stage input; time update after the last stage
+  for (int i = blockIdx.x; i < nsv; i += gridDim.x)
+    if (sv[i].sc->active) fin_alpha_block(sv[i].part_alpha, sv[i].part_cnt, (int)sv[i].ntiles, sv[i].sc, stage);
+}
+
+}  // namespace dg
+
+using namespace dg;
+
+struct dg_batch {
+  int n = 0, prec = 0;
+  std::vector<dg_solver *> solves;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  SolveDev *d_sv = nullptr;
+  WorkItem *d_work = nullptr;
+  BarrierState *d_bar = nullptr;
+  int nwork = 0, grid = 0, cpb = 0, max_blocks_per_sm = 0, blocks_per_sm = 0, num_sms = 0;
+  cudaGraphExec_t exec = nullptr;
+  bool graph_ok = false;
+  std::vector<SolveDev> host_sv;
+  ~dg_batch() {
+    if (stream) cudaStreamSynchronize(stream);
+    if (exec) cudaGraphExecDestroy(exec);
+    for (auto *s : solves) dg_solver_destroy(s);
+    cudaFree(d_sv);
+    cudaFree(d_work);
+    cudaFree(d_bar);
+    if (own_stream && stream) cudaStreamDestroy(stream);
+  }
+};
+
+namespace {
+
+const void *stage_kernel(int prec) {
+  return prec == DG_PREC_MIXED ? (const void *)k_batch_stage<float> : (const void *)k_batch_stage<double>;
+}
+
+cudaError_t launch_stage(dg_batch *b, int stage) {
+  int nsv = b->n, nwork = b->nwork;
+  void *args[] = {&b->d_sv, &nsv, &b->d_work, &nwork, &b->d_bar, &stage};
+  return cudaLaunchCooperativeKernel(stage_kernel(b->prec), dim3(b->grid), dim3(TPB), args, 0, b->stream);
+}
+
+// work list of chunks of cpb cells (cpb a multiple of TPB), solve after solve
+int32_t build_work(dg_batch *b, int cpb, int blocks_per_sm) {
+  std::vector<WorkItem> work;
+  const int64_t tpw = cpb / TPB;
+  for (int i = 0; i < b->n; ++i)
+    for (int64_t t = 0; t < b->host_sv[i].ntiles; t += tpw)
+      work.push_back(WorkItem{i, 0, t, std::min<int64_t>(tpw, b->host_sv[i].ntiles - t)});
+  cudaFree(b->d_work);
+  b->d_work = nullptr;
+  if (cudaMalloc(&b->d_work, sizeof(WorkItem) * work.size()) != cudaSuccess) return set_error(DG_ENOMEM, "work list");
+  if (cudaMemcpy(b->d_work, work.data(), sizeof(WorkItem) * work.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    return set_error(DG_ECUDA, "work list upload");
+  b->nwork = (int)work.size();
+  b->cpb = cpb;
+  b->blocks_per_sm = std::max(1, std::min(blocks_per_sm, b->max_blocks_per_sm));
+  b->grid = std::max(1, std::min(b->num_sms * b->blocks_per_sm, b->nwork));
+  // one SSP-RK3 step = three cooperative launches, captured as a graph when supported
+  if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+  b->graph_ok = false;
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+    cudaError_t e = cudaSuccess;
+    for (int st = 0; st < 3 && e == cudaSuccess; ++st) e = launch_stage(b, st);
+    cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+    if (e == cudaSuccess && e2 == cudaSuccess && g && cudaGraphInstantiate(&b->exec, g, 0) == cudaSuccess)
+      b->graph_ok = true;
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();   // a refused capture leaves an error behind: clear it
+  }
+  return DG_OK;
+}
+
+int32_t enqueue_steps(dg_batch *b, int64_t n) {
+  for (int64_t s = 0; s < n; ++s) {
+    if (b->graph_ok) {
+      if (cudaGraphLaunch(b->exec, b->stream) != cudaSuccess) return set_error(DG_ECUDA, "batch graph launch");
+    } else {
+      for (int st = 0; st < 3; ++st) {
+        cudaError_t e = launch_stage(b, st);
+        if (e != cudaSuccess) return set_error(DG_ECUDA, cudaGetErrorString(e));
+      }
+    }
+  }
+  return DG_OK;
+}
+
+int32_t check_barrier(dg_batch *b) {
+  BarrierState h{};
+  if (cudaMemcpyAsync(&h, b->d_bar, sizeof(h), cudaMemcpyDeviceToHost, b->stream) != cudaSuccess ||
+      cudaStreamSynchronize(b->stream) != cudaSuccess)
+    return set_error(DG_ECUDA, "batch sync");
+  if (h.error) {
+    BarrierState z{};
+    cudaMemcpy(b->d_bar, &z, sizeof(z), cudaMemcpyHostToDevice);
+    return set_error(DG_ETIMEOUT, "a grid barrier of the batch kernel timed out");
+  }
+  return DG_OK;
+}
+
+}  // namespace
+
+extern "C" int32_t dg_batch_create(int32_t n, const dg_mesh *const *meshes, const dg_config *cfgs,
+                                   const double *const *coeffs, void *cuda_stream, dg_batch **out) {
+  if (!out) return set_error(DG_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n <= 0 || !meshes || !cfgs || !coeffs) return set_error(DG_EINVAL, "empty batch or NULL arrays");
+  for (int i = 0; i < n; ++i)
+    if (cfgs[i].precision != cfgs[0].precision) return set_error(DG_EINVAL, "a batch has one precision");
+  auto b = new (std::nothrow) dg_batch();
+  if (!b) return set_error(DG_ENOMEM, "host allocation failed");
+  b->n = n;
+  b->prec = cfgs[0].precision;
+  if (cuda_stream) {
+    b->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete b;
+      return set_error(DG_ECUDA, "stream creation failed");
+    }
+    b->own_stream = true;
+  }
+  for (int i = 0; i < n; ++i) {
+    dg_solver *s = nullptr;
+    int32_t rc = dg_init(meshes[i], &cfgs[i], coeffs[i], b->stream, &s);
+    if (rc != DG_OK) { delete b; return rc; }
+    b->solves.push_back(s);
+    SolveDev d{};
+    const StageCtx &c = solver_ctx(s);
+    d.mesh = c.mesh;
+    d.ph = c.phys;
+    StateBuf un, uh, us;
+    solver_states(s, &un, &uh, &us);
+    d.avg[0] = un.avg; d.hi[0] = un.hi;
+    d.avg[1] = uh.avg; d.hi[1] = uh.hi;
+    d.avg[2] = us.avg; d.hi[2] = us.hi;
+    d.tr = c.tr; d.vd = c.vd; d.hs = c.hs;
+    d.part_sum = c.part_sum; d.part_dev = c.part_dev; d.part_alpha = c.part_alpha; d.part_cnt = c.part_cnt;
+    d.sc = c.sc;
+    d.k = cfgs[i].k;
+    d.oe = cfgs[i].oe;
+    d.bp = cfgs[i].bp;
+    d.ntiles = num_blocks(c.mesh.nt);
+    b->host_sv.push_back(d);
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  int coop = 0;
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (!coop) { delete b; return set_error(DG_EINVAL, "device does not support cooperative launches"); }
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->max_blocks_per_sm, stage_kernel(b->prec), TPB, 0) !=
+          cudaSuccess || b->max_blocks_per_sm < 1) {
+    delete b;
+    return set_error(DG_ECUDA, "occupancy query failed");
+  }
+  if (cudaMalloc(&b->d_sv, sizeof(SolveDev) * n) != cudaSuccess || cudaMalloc(&b->d_bar, sizeof(BarrierState)) != cudaSuccess) {
+    delete b;
+    return set_error(DG_ENOMEM, "batch descriptors");
+  }
+  BarrierState z{};
+  cudaMemcpy(b->d_sv, b->host_sv.data(), sizeof(SolveDev) * n, cudaMemcpyHostToDevice);
+  cudaMemcpy(b->d_bar, &z, sizeof(z), cudaMemcpyHostToDevice);
+  int32_t rc = build_work(b, 4 * TPB, b->max_blocks_per_sm);
+  if (rc != DG_OK) { delete b; return rc; }
+  *out = b;
+  return DG_OK;
+}
+
+extern "C" void dg_batch_destroy(dg_batch *b) { delete b; }
+
+extern "C" int32_t dg_batch_set_shape(dg_batch *b, int32_t cells_per_block, int32_t blocks_per_sm) {
+  if (!b || cells_per_block < TPB || cells_per_block % TPB != 0 || blocks_per_sm < 1)
+    return set_error(DG_EINVAL, "cells_per_block must be a positive multiple of 128, blocks_per_sm >= 1");
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return set_error(DG_ECUDA, "sync");
+  return build_work(b, cells_per_block, blocks_per_sm);
+}
+
+extern "C" int32_t dg_batch_shape(const dg_batch *b, int32_t *cells_per_block, int32_t *blocks_per_sm,
+                                  int32_t *grid, int32_t *graph) {
+  if (!b) return set_error(DG_EINVAL, "batch is NULL");
+  if (cells_per_block) *cells_per_block = b->cpb;
+  if (blocks_per_sm) *blocks_per_sm = b->blocks_per_sm;
+  if (grid) *grid = b->grid;
+  if (graph) *graph = b->graph_ok ? 1 : 0;
+  return DG_OK;
+}
+
+extern "C" int32_t dg_batch_advance_async(dg_batch *b, int64_t nsteps) {
+  if (!b || nsteps < 0) return set_error(DG_EINVAL, "bad argument");
+  return enqueue_steps(b, nsteps);
+}
+
+extern "C" int32_t dg_batch_advance(dg_batch *b, const double *t_end, int64_t max_steps, dg_stats *stats) {
+  if (!b || max_steps < 0) return set_error(DG_EINVAL, "bad argument");
+  std::vector<Scalars> h(b->n), start(b->n);
+  for (int i = 0; i < b->n; ++i) {
+    if (cudaMemcpyAsync(&h[i], b->host_sv[i].sc, sizeof(Scalars), cudaMemcpyDeviceToHost, b->stream) != cudaSuccess)
+      return set_error(DG_ECUDA, "scalars");
+  }
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return set_error(DG_ECUDA, "sync");
+  start = h;
+  for (int i = 0; i < b->n; ++i) {
+    h[i].t_end = t_end ? t_end[i] : INFINITY;
+    if (cudaMemcpyAsync(&b->host_sv[i].sc->t_end, &h[i].t_end, sizeof(double), cudaMemcpyHostToDevice, b->stream) !=
+        cudaSuccess)
+      return set_error(DG_ECUDA, "t_end");
+  }
+  int64_t done = 0;
+  auto unfinished = [&]() {
+    for (int i = 0; i < b->n; ++i)
+      if (h[i].t < h[i].t_end && std::isfinite(h[i].alpha) && h[i].alpha > 0.0) return true;
+    return false;
+  };
+  while (done < max_steps && unfinished()) {
+    const int64_t chunk = std::min<int64_t>(max_steps - done, 32);
+    int32_t rc = enqueue_steps(b, chunk);
+    if (rc != DG_OK) return rc;
+    done += chunk;
+    if ((rc = check_barrier(b)) != DG_OK) return rc;
+    for (int i = 0; i < b->n; ++i)
+      cudaMemcpyAsync(&h[i], b->host_sv[i].sc, sizeof(Scalars), cudaMemcpyDeviceToHost, b->stream);
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return set_error(DG_ECUDA, "sync");
+  }
+  int64_t bad = 0;
+  for (int i = 0; i < b->n; ++i) {
+    if (stats) {
+      stats[i].steps = h[i].steps - start[i].steps;
+      stats[i].limited_cells = h[i].limited - start[i].limited;
+      stats[i].nonphysical = h[i].nonphys - start[i].nonphys;
+      stats[i].cfl_breaches = h[i].breaches - start[i].breaches;
+      stats[i].t = h[i].t;
+      stats[i].dt_last = h[i].dt;
+      stats[i].alpha = h[i].alpha;
+    }
+    bad += h[i].nonphys - start[i].nonphys;
+  }
+  if (bad > 0) return set_error(DG_ENONPHYS, "cell averages left the admissible set in the batch");
+  return DG_OK;
+}
+
+extern "C" int32_t dg_batch_sync(dg_batch *b) {
+  if (!b) return set_error(DG_EINVAL, "batch is NULL");
+  return check_barrier(b);
+}
+
+extern "C" int32_t dg_batch_solver(dg_batch *b, int32_t i, dg_solver **out) {
+  if (!b || !out || i < 0 || i >= b->n) return set_error(DG_EINVAL, "bad index");
+  *out = b->solves[i];
+  return DG_OK;
+}
+
+extern "C" int32_t dg_batch_autotune(dg_batch *b, int32_t steps, int32_t *best_cpb, int32_t *best_bpsm,
+                                     double *best_ms) {
+  if (!b || steps < 1) return set_error(DG_EINVAL, "bad argument");
+  // snapshot every solve's device state (averages, modes, traces of u_n and
+  // scalars); restoring these bytes undoes the tuning steps exactly
+  struct Snap { void *avg, *hi, *tr; size_t navg, nhi, ntr; Scalars sc; };
+  std::vector<Snap> snaps(b->n);
+  const size_t rs = b->prec == DG_PREC_MIXED ? sizeof(float) : sizeof(double);
+  auto free_snaps = [&]() { for (auto &q : snaps) { cudaFree(q.avg); cudaFree(q.hi); cudaFree(q.tr); } };
+  for (int i = 0; i < b->n; ++i) {
+    dg_solver *s = b->solves[i];
+    const int64_t nt = solver_ctx(s).mesh.nt;
+    const int nb = solver_nb(s), nq = nb == 3 ? 2 : 3;
+    StateBuf un, uh, us;
+    solver_states(s, &un, &uh, &us);
+    Snap &q = snaps[i];
+    q = Snap{nullptr, nullptr, nullptr, sizeof(double) * 4 * nt, rs * 4 * (nb - 1) * nt, rs * nt * 3 * nq * 8, {}};
+    if (cudaMalloc(&q.avg, q.navg) != cudaSuccess || cudaMalloc(&q.hi, q.nhi) != cudaSuccess ||
+        cudaMalloc(&q.tr, q.ntr) != cudaSuccess) {
+      free_snaps();
+      return set_error(DG_ENOMEM, "autotune snapshot");
+    }
+    cudaMemcpyAsync(q.avg, un.avg, q.navg, cudaMemcpyDeviceToDevice, b->stream);
+    cudaMemcpyAsync(q.hi, un.hi, q.nhi, cudaMemcpyDeviceToDevice, b->stream);
+    cudaMemcpyAsync(q.tr, solver_ctx(s).tr, q.ntr, cudaMemcpyDeviceToDevice, b->stream);
+    if (solver_read_scalars(s, &q.sc) != DG_OK) { free_snaps(); return DG_ECUDA; }
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double best = INFINITY;
+  int bc = b->cpb, bb = b->blocks_per_sm;
+  const int cpbs[4] = {TPB, 2 * TPB, 4 * TPB, 8 * TPB};
+  for (int ci = 0; ci < 4; ++ci)
+    for (int bpsm = 1; bpsm <= b->max_blocks_per_sm; ++bpsm) {
+      int32_t rc = build_work(b, cpbs[ci], bpsm);
+      if (rc == DG_OK) rc = enqueue_steps(b, 1);   // warm-up
+      cudaEventRecord(e0, b->stream);
+      if (rc == DG_OK) rc = enqueue_steps(b, steps);
+      cudaEventRecord(e1, b->stream);
+      if (rc == DG_OK) rc = check_barrier(b);
+      if (rc != DG_OK) { free_snaps(); return rc; }
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) { best = ms; bc = cpbs[ci]; bb = bpsm; }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (int i = 0; i < b->n; ++i) {
+    dg_solver *s = b->solves[i];
+    StateBuf un, uh, us;
+    solver_states(s, &un, &uh, &us);
+    const Snap &q = snaps[i];
+    cudaMemcpyAsync(un.avg, q.avg, q.navg, cudaMemcpyDeviceToDevice, b->stream);
+    cudaMemcpyAsync(un.hi, q.hi, q.nhi, cudaMemcpyDeviceToDevice, b->stream);
+    cudaMemcpyAsync(solver_ctx(s).tr, q.tr, q.ntr, cudaMemcpyDeviceToDevice, b->stream);
+    if (solver_write_scalars(s, &q.sc) != DG_OK) { free_snaps(); return DG_ECUDA; }
+  }
+  free_snaps();
+  int32_t rc = build_work(b, bc, bb);
+  if (rc != DG_OK) return rc;
+  if (best_cpb) *best_cpb = bc;
+  if (best_bpsm) *best_bpsm = bb;
+  if (best_ms) *best_ms = best / steps;
+  return DG_OK;
+}

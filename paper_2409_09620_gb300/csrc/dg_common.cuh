@@ -241,11 +241,114 @@ __device__ __forceinline__ void block_reduce(T v[N], T *out, Op op) {
       out[q] = s;
     }
   }
+  __syncthreads();   // red[] may be reused by the next call of this block
+}
+
+// Fixed-order reduction of nblk partials of N values by one block: FIN_THREADS
+// virtual lanes each reduce a strided subset, then a fixed tree.  The
+// arithmetic does not depend on the block size, so a persistent kernel with
+// TPB threads reproduces the FIN_THREADS-thread finalize kernels bitwise.
+template <int N, typename T, typename Op>
+__device__ void fin_reduce(const T *part, int nblk, T init, Op op, T out[N]) {
+  __shared__ T sh[FIN_THREADS][N];
+  for (int vt = threadIdx.x; vt < FIN_THREADS; vt += blockDim.x) {
+    T acc[N];
+#pragma unroll
+    for (int q = 0; q < N; ++q) acc[q] = init;
+    for (int b = vt; b < nblk; b += FIN_THREADS)
+#pragma unroll
+      for (int q = 0; q < N; ++q) acc[q] = op(acc[q], part[b * N + q]);
+#pragma unroll
+    for (int q = 0; q < N; ++q) sh[vt][q] = acc[q];
+  }
+  __syncthreads();
+  for (int st = FIN_THREADS / 2; st > 0; st >>= 1) {
+    for (int vt = threadIdx.x; vt < st; vt += blockDim.x)
+#pragma unroll
+      for (int q = 0; q < N; ++q) sh[vt][q] = op(sh[vt][q], sh[vt + st][q]);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < N; ++q) out[q] = sh[0][q];
+  __syncthreads();
 }
 
 struct OpSum { template <typename T> __device__ T operator()(T a, T b) const { return a + b; } };
 struct OpMax {
   __device__ double operator()(double a, double b) const { return (a > b || a != a) ? a : b; }
 };
+
+// ------------------------------------------------------------------------
+// Per-solve finalize steps (one block; thread 0 writes the scalars)
+// ------------------------------------------------------------------------
+// 1 / D_q of the damped quantities from sc->dev and sc->mean (eqs.
+// OEScalar:Coef2, RIOESys:Coef1/Coef2 with the round-off guard of Sec. 2.3:
+// a component whose deviation is below 1e-12 max(1, |mean|) is constant)
+__device__ __forceinline__ void write_inv_normalisers(Scalars *sc, int cw) {
+  const double eps = 1e-12;
+  auto inv = [&](double D, double ref) { return D <= eps * fmax(1.0, ref) ? 0.0 : 1.0 / D; };
+  sc->invD[0] = inv(sc->dev[0], fabs(sc->mean[0]));
+  sc->invD[3] = inv(sc->dev[2], fabs(sc->mean[3]));
+  if (cw) {
+    sc->invD[1] = inv(sc->dev[3], fabs(sc->mean[1]));
+    sc->invD[2] = inv(sc->dev[4], fabs(sc->mean[2]));
+  } else {
+    const double mnorm = sqrt(sc->mean[1] * sc->mean[1] + sc->mean[2] * sc->mean[2]);
+    sc->invD[1] = sc->invD[2] = inv(sc->dev[1], mnorm);
+  }
+}
+
+// domain means of u_h from the block sums of |K| u_h^(0)
+__device__ __forceinline__ void fin_mean_block(const double *part, int nblk, Scalars *sc) {
+  double r[4];
+  fin_reduce<4>(part, nblk, 0.0, OpSum(), r);
+  if (threadIdx.x == 0)
+    for (int c = 0; c < 4; ++c) sc->mean[c] = r[c] / sc->area_total;
+}
+
+// sup deviations, then the reciprocal OE normalisers
+__device__ __forceinline__ void fin_dev_block(const double *part, int nblk, Scalars *sc, int cw) {
+  double r[5];
+  fin_reduce<5>(part, nblk, 0.0, OpMax(), r);
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < 5; ++q) sc->dev[q] = r[q];
+    write_inv_normalisers(sc, cw);
+  }
+}
+
+// alpha of the new stage input and counters; after the last stage, t += dt
+__device__ __forceinline__ void fin_alpha_block(const double *pa, const long long *pc, int nblk, Scalars *sc,
+                                                int stage) {
+  double a[1];
+  fin_reduce<1>(pa, nblk, 0.0, OpMax(), a);
+  long long c[2];
+  fin_reduce<2>(pc, nblk, 0LL, OpSum(), c);
+  if (threadIdx.x == 0) {
+    sc->alpha = a[0];
+    sc->limited += c[0];
+    sc->nonphys += c[1];
+    if (stage == 0 || stage == 1) {
+      if (a[0] * sc->dt > sc->min_ca * (1.0 + 1e-12)) sc->breaches += 1;
+    } else if (stage == 2) {
+      sc->t = sc->pad ? sc->t_end : sc->t + sc->dt;
+      sc->steps += 1;
+    }
+  }
+}
+
+// dt of the BP CFL condition (Sec. 5), clamped to t_end; inactive once t >= t_end
+__device__ __forceinline__ void step_begin_thread(Scalars *sc) {
+  if (sc->t < sc->t_end) {
+    double dt = sc->cfl * sc->min_ca / sc->alpha;
+    int clamped = 0;
+    if (sc->t + dt >= sc->t_end) { dt = sc->t_end - sc->t; clamped = 1; }
+    sc->dt = dt;
+    sc->pad = clamped;
+    sc->active = 1;
+  } else {
+    sc->dt = 0.0;
+    sc->active = 0;
+  }
+}
 
 }  // namespace dg

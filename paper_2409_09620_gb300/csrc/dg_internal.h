@@ -52,6 +52,13 @@ void launch_set_active(const StageCtx &c, int active);
 void launch_set_inv_normalisers(const StageCtx &c);
 int64_t num_blocks(int64_t nt);
 
+// access to a solver's launch context and buffers (dg_api.cu)
+const StageCtx &solver_ctx(const dg_solver *s);
+void solver_states(const dg_solver *s, StateBuf *un, StateBuf *uh, StateBuf *us);
+int solver_nb(const dg_solver *s);
+int32_t solver_read_scalars(const dg_solver *s, Scalars *h);
+int32_t solver_write_scalars(dg_solver *s, const Scalars *h);
+
 // mesh size, device cell areas and their host-summed total (dg_api.cu)
 void mesh_view(const dg_mesh *mesh, int64_t *nt, const double **area, double *area_total);
 // record a message for dg_last_error and return code (dg_api.cu)

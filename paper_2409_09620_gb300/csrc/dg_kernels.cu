@@ -86,47 +86,9 @@ __global__ void __launch_bounds__(TPB) k_geometry(int64_t nt, const double *__re
   block_reduce<4>(mins, part_min + 4 * blockIdx.x, OpMinD());
 }
 
-// 1 / D_q of the damped quantities from sc->dev and sc->mean (eqs.
-// OEScalar:Coef2, RIOESys:Coef1/Coef2 with the round-off guard of Sec. 2.3)
-__device__ void write_inv_normalisers(Scalars *sc, int cw) {
-  const double eps = 1e-12;
-  auto inv = [&](double D, double ref) { return D <= eps * fmax(1.0, ref) ? 0.0 : 1.0 / D; };
-  sc->invD[0] = inv(sc->dev[0], fabs(sc->mean[0]));
-  sc->invD[3] = inv(sc->dev[2], fabs(sc->mean[3]));
-  if (cw) {
-    sc->invD[1] = inv(sc->dev[3], fabs(sc->mean[1]));
-    sc->invD[2] = inv(sc->dev[4], fabs(sc->mean[2]));
-  } else {
-    const double mnorm = sqrt(sc->mean[1] * sc->mean[1] + sc->mean[2] * sc->mean[2]);
-    sc->invD[1] = sc->invD[2] = inv(sc->dev[1], mnorm);
-  }
-}
-
 // ==========================================================================
 // Fixed-order reductions of block partials (one block)
 // ==========================================================================
-template <int N, typename T, typename Op>
-__device__ void fin_reduce(const T *part, int nblk, T init, Op op, T out[N]) {
-  __shared__ T sh[FIN_THREADS][N];
-  T acc[N];
-#pragma unroll
-  for (int q = 0; q < N; ++q) acc[q] = init;
-  for (int b = threadIdx.x; b < nblk; b += FIN_THREADS)
-#pragma unroll
-    for (int q = 0; q < N; ++q) acc[q] = op(acc[q], part[b * N + q]);
-#pragma unroll
-  for (int q = 0; q < N; ++q) sh[threadIdx.x][q] = acc[q];
-  __syncthreads();
-  for (int s = FIN_THREADS / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s)
-#pragma unroll
-      for (int q = 0; q < N; ++q) sh[threadIdx.x][q] = op(sh[threadIdx.x][q], sh[threadIdx.x + s][q]);
-    __syncthreads();
-  }
-#pragma unroll
-  for (int q = 0; q < N; ++q) out[q] = sh[0][q];
-}
-
 __global__ void k_fin_min4(const double *part, int nblk, double *out) {
   double r[4];
   fin_reduce<4>(part, nblk, (double)INFINITY, OpMinD(), r);
@@ -136,59 +98,23 @@ __global__ void k_fin_min4(const double *part, int nblk, double *out) {
 
 __global__ void k_fin_mean(const double *part, int nblk, Scalars *sc) {
   if (!sc->active) return;
-  double r[4];
-  fin_reduce<4>(part, nblk, 0.0, OpSum(), r);
-  if (threadIdx.x == 0)
-    for (int c = 0; c < 4; ++c) sc->mean[c] = r[c] / sc->area_total;
+  fin_mean_block(part, nblk, sc);
 }
 
 // sup deviations, then the reciprocal normalisers of the OE: a component whose
 // deviation is below 1e-12 max(1, |mean|) counts as constant (delta = 0)
 __global__ void k_fin_dev(const double *part, int nblk, Scalars *sc, int cw) {
   if (!sc->active) return;
-  double r[5];
-  fin_reduce<5>(part, nblk, 0.0, OpMax(), r);
-  if (threadIdx.x == 0) {
-    for (int q = 0; q < 5; ++q) sc->dev[q] = r[q];
-    write_inv_normalisers(sc, cw);
-  }
+  fin_dev_block(part, nblk, sc, cw);
 }
 
-// alpha of the new stage input and counters; after the last stage, t += dt
 __global__ void k_fin_alpha(const double *pa, const long long *pc, int nblk, Scalars *sc, int stage) {
   if (!sc->active) return;
-  double a[1];
-  fin_reduce<1>(pa, nblk, 0.0, OpMax(), a);
-  __syncthreads();
-  long long c[2];
-  fin_reduce<2>(pc, nblk, 0LL, OpSum(), c);
-  if (threadIdx.x == 0) {
-    sc->alpha = a[0];
-    sc->limited += c[0];
-    sc->nonphys += c[1];
-    if (stage == 0 || stage == 1) {
-      if (a[0] * sc->dt > sc->min_ca * (1.0 + 1e-12)) sc->breaches += 1;
-    } else if (stage == 2) {
-      sc->t = sc->pad ? sc->t_end : sc->t + sc->dt;
-      sc->steps += 1;
-    }
-  }
+  fin_alpha_block(pa, pc, nblk, sc, stage);
 }
 
-// dt of the BP CFL condition (Sec. 5), clamped to t_end; inactive once t >= t_end
 __global__ void k_step_begin(Scalars *sc) {
-  if (threadIdx.x != 0) return;
-  if (sc->t < sc->t_end) {
-    double dt = sc->cfl * sc->min_ca / sc->alpha;
-    int clamped = 0;
-    if (sc->t + dt >= sc->t_end) { dt = sc->t_end - sc->t; clamped = 1; }
-    sc->dt = dt;
-    sc->pad = clamped;
-    sc->active = 1;
-  } else {
-    sc->dt = 0.0;
-    sc->active = 0;
-  }
+  if (threadIdx.x == 0) step_begin_thread(sc);
 }
 
 __global__ void k_set_inv_normalisers(Scalars *sc, int cw) {

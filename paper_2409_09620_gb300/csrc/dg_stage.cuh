@@ -43,16 +43,16 @@ __device__ __forceinline__ void eval_fixed(const double avg[4], const Real hi[4]
 // ==========================================================================
 // K1: u_h = a u_n + b (v + dt L(v))
 // ==========================================================================
+// one tile of TPB cells starting at cell tile * TPB; block partial -> part_sum[4 * tile]
 template <int K, typename Real>
-__global__ void __launch_bounds__(TPB) k_rk(MeshDev m, Phys ph, StateDev<Real> v, StateDev<Real> un,
-                                            StateDev<Real> uh, const Real *__restrict__ tr,
-                                            Real *__restrict__ vdo, Real *__restrict__ hso,
-                                            double *__restrict__ part_sum, const Scalars *__restrict__ sc,
-                                            double a, double b, double c_in) {
+__device__ __forceinline__ void rk_tile(const MeshDev &m, const Phys &ph, StateDev<Real> v, StateDev<Real> un,
+                                        StateDev<Real> uh, const Real *__restrict__ tr, Real *__restrict__ vdo,
+                                        Real *__restrict__ hso, double *__restrict__ part_sum,
+                                        const Scalars *__restrict__ sc, double a, double b, double c_in,
+                                        int64_t tile) {
   constexpr int NB = Deg<K>::NB, NQ = Deg<K>::NQ, NV = Deg<K>::NV;
-  if (!sc->active) return;
   const int64_t nt = m.nt;
-  const int64_t Kc = (int64_t)blockIdx.x * TPB + threadIdx.x;
+  const int64_t Kc = tile * TPB + threadIdx.x;
   double mass[4] = {0.0, 0.0, 0.0, 0.0};
   if (Kc < nt) {
     const double dt = sc->dt, alpha_d = sc->alpha, t_in = sc->t + c_in * sc->dt;
@@ -209,19 +209,28 @@ __global__ void __launch_bounds__(TPB) k_rk(MeshDev m, Phys ph, StateDev<Real> v
       }
     }
   }
-  block_reduce<4>(mass, part_sum + 4 * blockIdx.x, OpSum());
+  block_reduce<4>(mass, part_sum + 4 * tile, OpSum());
+}
+
+template <int K, typename Real>
+__global__ void __launch_bounds__(TPB) k_rk(MeshDev m, Phys ph, StateDev<Real> v, StateDev<Real> un,
+                                            StateDev<Real> uh, const Real *__restrict__ tr,
+                                            Real *__restrict__ vdo, Real *__restrict__ hso,
+                                            double *__restrict__ part_sum, const Scalars *__restrict__ sc,
+                                            double a, double b, double c_in) {
+  if (!sc->active) return;
+  rk_tile<K, Real>(m, ph, v, un, uh, tr, vdo, hso, part_sum, sc, a, b, c_in, blockIdx.x);
 }
 
 // ==========================================================================
 // K2: sup deviations from the domain mean at the volume points
 // ==========================================================================
 template <int K, typename Real>
-__global__ void __launch_bounds__(TPB) k_stats(MeshDev m, StateDev<Real> uh, double *__restrict__ part_dev,
-                                               const Scalars *__restrict__ sc) {
+__device__ __forceinline__ void stats_tile(const MeshDev &m, StateDev<Real> uh, double *__restrict__ part_dev,
+                                           const Scalars *__restrict__ sc, int64_t tile) {
   constexpr int NB = Deg<K>::NB, NV = Deg<K>::NV;
-  if (!sc->active) return;
   const int64_t nt = m.nt;
-  const int64_t Kc = (int64_t)blockIdx.x * TPB + threadIdx.x;
+  const int64_t Kc = tile * TPB + threadIdx.x;
   double d[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
   if (Kc < nt) {
     double a0[4];
@@ -243,7 +252,14 @@ __global__ void __launch_bounds__(TPB) k_stats(MeshDev m, StateDev<Real> uh, dou
       d[4] = fmax(d[4], fabs(double(u[2])));
     }
   }
-  block_reduce<5>(d, part_dev + 5 * blockIdx.x, OpMax());
+  block_reduce<5>(d, part_dev + 5 * tile, OpMax());
+}
+
+template <int K, typename Real>
+__global__ void __launch_bounds__(TPB) k_stats(MeshDev m, StateDev<Real> uh, double *__restrict__ part_dev,
+                                               const Scalars *__restrict__ sc) {
+  if (!sc->active) return;
+  stats_tile<K, Real>(m, uh, part_dev, sc, blockIdx.x);
 }
 
 // ==========================================================================
@@ -533,16 +549,15 @@ __device__ __forceinline__ void limit_and_trace_mixed(const MeshDev &m, const Ph
 }
 
 template <int K, typename Real>
-__global__ void __launch_bounds__(TPB) k_oe_bp(MeshDev m, Phys ph, StateDev<Real> uh, StateDev<Real> out,
-                                               const Real *__restrict__ vdi, const Real *__restrict__ hsi,
-                                               Real *__restrict__ tr, double *__restrict__ part_alpha,
-                                               long long *__restrict__ part_cnt, const Scalars *__restrict__ sc,
-                                               int do_oe, int do_bp, double c_out) {
+__device__ __forceinline__ void oe_bp_tile(const MeshDev &m, const Phys &ph, StateDev<Real> uh, StateDev<Real> out,
+                                           const Real *__restrict__ vdi, const Real *__restrict__ hsi,
+                                           Real *__restrict__ tr, double *__restrict__ part_alpha,
+                                           long long *__restrict__ part_cnt, const Scalars *__restrict__ sc,
+                                           int do_oe, int do_bp, double c_out, int64_t tile) {
   constexpr int NB = Deg<K>::NB, NQ = Deg<K>::NQ;
   constexpr int NE = 3 * NQ;          // edge Gauss points
-  if (!sc->active) return;
   const int64_t nt = m.nt;
-  const int64_t Kc = (int64_t)blockIdx.x * TPB + threadIdx.x;
+  const int64_t Kc = tile * TPB + threadIdx.x;
   double amax = 0.0;
   long long cnt[2] = {0, 0};
   if (Kc < nt) {
@@ -814,10 +829,21 @@ __global__ void __launch_bounds__(TPB) k_oe_bp(MeshDev m, Phys ph, StateDev<Real
     }
   }
   double av[1] = {amax};
-  block_reduce<1>(av, part_alpha + blockIdx.x, OpMax());
+  block_reduce<1>(av, part_alpha + tile, OpMax());
   __syncthreads();
   long long cv[2] = {cnt[0], cnt[1]};
-  block_reduce<2>(cv, part_cnt + 2 * blockIdx.x, OpSum());
+  block_reduce<2>(cv, part_cnt + 2 * tile, OpSum());
+  __syncthreads();
+}
+
+template <int K, typename Real>
+__global__ void __launch_bounds__(TPB) k_oe_bp(MeshDev m, Phys ph, StateDev<Real> uh, StateDev<Real> out,
+                                               const Real *__restrict__ vdi, const Real *__restrict__ hsi,
+                                               Real *__restrict__ tr, double *__restrict__ part_alpha,
+                                               long long *__restrict__ part_cnt, const Scalars *__restrict__ sc,
+                                               int do_oe, int do_bp, double c_out) {
+  if (!sc->active) return;
+  oe_bp_tile<K, Real>(m, ph, uh, out, vdi, hsi, tr, part_alpha, part_cnt, sc, do_oe, do_bp, c_out, blockIdx.x);
 }
 
 }  // namespace dg

@@ -68,6 +68,15 @@ SIGNATURES = {
     "dg_op_alpha": (i32, [P, P, dbl, C.POINTER(dbl)]),
     "dg_profile_steps": (i32, [P, i64, P, P]),
     "dg_stats_noalloc": (i32, [P, i32, P, P, P]),
+    "dg_batch_create": (i32, [i32, P, P, P, P, C.POINTER(P)]),
+    "dg_batch_destroy": (None, [P]),
+    "dg_batch_advance": (i32, [P, P, i64, P]),
+    "dg_batch_advance_async": (i32, [P, i64]),
+    "dg_batch_sync": (i32, [P]),
+    "dg_batch_solver": (i32, [P, i32, C.POINTER(P)]),
+    "dg_batch_set_shape": (i32, [P, i32, i32]),
+    "dg_batch_shape": (i32, [P, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
+    "dg_batch_autotune": (i32, [P, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(dbl)]),
     "dg_last_error": (C.c_char_p, []),
 }
 
@@ -284,6 +293,74 @@ class Solver:
         a = dbl()
         _check(lib().dg_op_alpha(self.h, _p(u), t, C.byref(a)))
         return a.value
+
+
+class _SolverView(Solver):
+    """A solver owned by a batch (not destroyed by Python)."""
+
+    def __init__(self, mesh, cfg, h):
+        self.mesh, self.cfg, self.nb, self.h = mesh, cfg, (3 if cfg.k == 1 else 6), h
+
+    def close(self):
+        self.h = None
+
+
+class Batch:
+    """dg_batch handle: independent solves advanced by one persistent launch per stage."""
+
+    def __init__(self, meshes, cfgs, coeffs, stream=None):
+        n = len(meshes)
+        self.meshes, self.cfgs = list(meshes), list(cfgs)
+        self._u = [np.ascontiguousarray(u, np.float64) for u in coeffs]
+        mh = (P * n)(*[m.h for m in meshes])
+        cf = (Config * n)(*cfgs)
+        up = (P * n)(*[_p(u) for u in self._u])
+        h = P()
+        _check(lib().dg_batch_create(n, C.cast(mh, P), C.cast(cf, P), C.cast(up, P),
+                                     None if stream is None else P(stream), C.byref(h)))
+        self.h = h
+        self.n = n
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().dg_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solver(self, i):
+        s = P()
+        _check(lib().dg_batch_solver(self.h, i, C.byref(s)))
+        return _SolverView(self.meshes[i], self.cfgs[i], s)
+
+    def advance(self, t_end=None, max_steps=1 << 62):
+        te = None if t_end is None else np.ascontiguousarray(np.broadcast_to(t_end, (self.n,)), np.float64)
+        st = (Stats * self.n)()
+        _check(lib().dg_batch_advance(self.h, _p(te), max_steps, C.cast(st, P)))
+        return [s.as_dict() for s in st]
+
+    def advance_async(self, n):
+        _check(lib().dg_batch_advance_async(self.h, n))
+
+    def sync(self):
+        _check(lib().dg_batch_sync(self.h))
+
+    def set_shape(self, cells_per_block, blocks_per_sm):
+        _check(lib().dg_batch_set_shape(self.h, cells_per_block, blocks_per_sm))
+
+    def shape(self):
+        a, b, g, gr = i32(), i32(), i32(), i32()
+        _check(lib().dg_batch_shape(self.h, C.byref(a), C.byref(b), C.byref(g), C.byref(gr)))
+        return dict(cells_per_block=a.value, blocks_per_sm=b.value, grid=g.value, graph=bool(gr.value))
+
+    def autotune(self, steps=3):
+        a, b, ms = i32(), i32(), dbl()
+        _check(lib().dg_batch_autotune(self.h, steps, C.byref(a), C.byref(b), C.byref(ms)))
+        return dict(cells_per_block=a.value, blocks_per_sm=b.value, ms_per_step=ms.value)
 
 
 def initial_state(mesh: Mesh, workload):

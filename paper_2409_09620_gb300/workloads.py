@@ -310,3 +310,18 @@ def random_modal_state(nt: int, k: int, seed: int, mean=(1.0, 0.2, -0.1, 2.5),
     u[:, 0, :] = mean[:, None] * (1.0 + mean_jitter * rng.uniform(-1, 1, (4, nt)))
     u[:, 1:, :] = amp * np.abs(mean)[:, None, None] * rng.uniform(-1, 1, (4, nb - 1, nt))
     return u
+
+
+def batch_workloads(n=64, seed=7, cmin=2000, cmax=200000):
+    """Independent solves of the batch benchmark: P1 or P2 (seeded 50/50),
+    cell counts log-uniform in [cmin, cmax] (unit square, n x n squares split
+    in two), four-quadrant Riemann data with per-solve seeded states,
+    transmissive boundaries."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        k = int(rng.integers(1, 3))
+        cells = math.exp(rng.uniform(math.log(cmin), math.log(cmax)))
+        side = max(4, int(round(math.sqrt(cells / 2.0))))
+        out.append(riemann4_workload(n=side, k=k, seed=seed * 1000 + i))
+    return out
