@@ -224,6 +224,9 @@ def main():
     ap.add_argument("--profile-steps", type=int, default=10)
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=10)
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--serve-rate", type=float, default=30.0)
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -370,6 +373,45 @@ def main():
                             "ms_per_step": bms / args.batch_steps, "shape": bt.shape(), "autotune": tune}
             del bt
 
+    # serving: Poisson arrivals of solve requests, continuous batching
+    serving = None
+    if not args.no_serving:
+        from paper_2409_09620_gb300 import workloads as W
+        reqs = W.serving_requests(args.serve_requests, rate=args.serve_rate)
+        payload = []
+        for wl_r, te, at in reqs:
+            m = N.Mesh.from_mesh(wl_r.mesh)
+            payload.append((wl_r, N.config_for(wl_r), N.initial_state(m, wl_r), te, at))
+            m.close()
+        srv = N.Server(N.PREC_FP64, budget_bytes=32 << 30, steps_per_tick=4)
+        barrier(world)
+        t0 = time.perf_counter()
+        ids, nxt, max_run = [], 0, 0
+        while True:
+            now = time.perf_counter() - t0
+            while nxt < len(payload) and payload[nxt][4] <= now:
+                wl_r, cf_r, u_r, te, _ = payload[nxt]
+                ids.append(srv.submit(wl_r.mesh, cf_r, u_r, te))
+                nxt += 1
+            r, q = srv.tick()
+            max_run = max(max_run, r)
+            if r == 0 and q == 0:
+                if nxt == len(payload):
+                    break
+                time.sleep(max(0.0, payload[nxt][4] - (time.perf_counter() - t0)))
+        makespan = dist_max(time.perf_counter() - t0, world)
+        infos = [srv.info(i) for i in ids]
+        lat = np.array([f["done_s"] - f["submit_s"] for f in infos])
+        done_cells = sum(f["cells"] * 3 * f["steps"] for f in infos)
+        serving = {"requests": len(ids), "rate_per_s": args.serve_rate, "precision": "fp64",
+                   "failed": int(sum(f["state"] != N.REQ_DONE for f in infos)),
+                   "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+                   "mean_latency_s": float(lat.mean()), "makespan_s": makespan,
+                   "throughput": done_cells * world / makespan, "unit": UNIT, "max_running": max_run,
+                   "cells_range": [int(min(f["cells"] for f in infos)), int(max(f["cells"] for f in infos))],
+                   "steps_total": int(sum(f["steps"] for f in infos))}
+        srv.close()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         wl_full = make_workload(args.workload, args.nx, args.ny)
@@ -388,6 +430,7 @@ def main():
                            "l2": "working set ~1.7 GB > 129 MB L2, no flush"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": 19 * args.steps, "clocks": clocks, "fp32": mixed, "batch": batch,
+                "serving": serving,
                 "peaks": {"source": peak_src, "hbm_gbs": peaks.get("hbm_gbs")},
                 "stats": {"limited_cells": st["limited_cells"], "cfl_breaches": st["cfl_breaches"],
                           "t": st["t"], "dt_last": st["dt_last"]}}

@@ -61,6 +61,7 @@ extern "C" {
 typedef struct dg_mesh dg_mesh;
 typedef struct dg_solver dg_solver;
 typedef struct dg_batch dg_batch;
+typedef struct dg_server dg_server;
 
 typedef struct dg_config {
   int32_t k;              /* polynomial degree: 1 or 2 */
@@ -230,6 +231,51 @@ int32_t dg_batch_shape(const dg_batch *batch, int32_t *cells_per_block, int32_t 
  * result (partials are per 128 cells of each solve). */
 int32_t dg_batch_autotune(dg_batch *batch, int32_t steps, int32_t *best_cells_per_block,
                           int32_t *best_blocks_per_sm, double *best_ms_per_step);
+
+/* ---------------------------------------------------------------------- */
+/* Serving: continuous batching of independent solve requests               */
+/* ---------------------------------------------------------------------- */
+
+#define DG_REQ_QUEUED 0
+#define DG_REQ_RUNNING 1
+#define DG_REQ_DONE 2
+#define DG_REQ_FAILED 3
+
+typedef struct dg_request_info {
+  int32_t state;          /* DG_REQ_* */
+  int32_t error;          /* status of a failed request (DG_ENOMEM: larger than the budget) */
+  int64_t cells;
+  int64_t steps;          /* time steps taken so far */
+  double t, t_end;
+  double submit_s;        /* server clock (s) at submission, admission and completion */
+  double start_s;
+  double done_s;
+  int64_t device_bytes;   /* device memory charged against the budget while running */
+} dg_request_info;
+
+/* Create a server of solves in one precision with an HBM budget (bytes of
+ * device memory its running solves may hold) and a number of time steps per
+ * tick; work goes to cuda_stream (NULL = a stream the server creates). */
+int32_t dg_server_create(int32_t precision, size_t hbm_budget_bytes, int32_t steps_per_tick,
+                         void *cuda_stream, dg_server **out);
+void dg_server_destroy(dg_server *server);
+/* Queue a solve: host mesh arrays (as dg_mesh_create), configuration, host
+ * initial coefficients and end time are copied; *id identifies the request. */
+int32_t dg_server_submit(dg_server *server, int64_t nv, const double *xy, int64_t nt, const int32_t *tri,
+                         const int32_t *canon, const int8_t *bc, const dg_config *cfg, const double *coeffs,
+                         double t_end, int64_t *id);
+/* One scheduling round: wait for the steps of the previous round; retire
+ * solves that reached their end time (result copied to the host, device memory
+ * released); admit queued requests in order while they fit in the budget
+ * (mesh built, initial limiter applied); enqueue steps_per_tick steps of every
+ * running solve in one persistent launch per stage and return without waiting
+ * for them.  A request larger than the whole budget fails with DG_ENOMEM. */
+int32_t dg_server_tick(dg_server *server, int32_t *n_running, int32_t *n_queued);
+int32_t dg_server_request(const dg_server *server, int64_t id, dg_request_info *info);
+/* host copy of a finished request's coefficients (layout as dg_get_state) */
+int32_t dg_server_result(dg_server *server, int64_t id, double *coeffs, size_t len);
+/* device bytes held by running solves; cell-stage updates of retired solves */
+int32_t dg_server_stats(const dg_server *server, int64_t *bytes_in_use, int64_t *cell_stages_done);
 
 /* ---------------------------------------------------------------------- */
 /* Statistics without device allocation                                    */

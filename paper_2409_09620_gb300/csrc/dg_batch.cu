@@ -161,101 +161,178 @@ __global__ void __launch_bounds__(TPB) k_batch_stage(const SolveDev *__restrict_
 
 using namespace dg;
 
-struct dg_batch {
-  int n = 0, prec = 0;
-  std::vector<dg_solver *> solves;
+namespace dg {
+
+// A set of solves advanced together by the persistent stage kernel.  The set
+// can change between steps (set_solves): the solve descriptors, the work list
+// and the step graph are rebuilt.
+struct BatchCore {
+  int prec = 0;
   cudaStream_t stream = nullptr;
-  bool own_stream = false;
+  std::vector<dg_solver *> solves;
+  std::vector<SolveDev> host_sv;
   SolveDev *d_sv = nullptr;
+  size_t sv_cap = 0;
   WorkItem *d_work = nullptr;
+  size_t work_cap = 0;
   BarrierState *d_bar = nullptr;
-  int nwork = 0, grid = 0, cpb = 0, max_blocks_per_sm = 0, blocks_per_sm = 0, num_sms = 0;
+  int nwork = 0, grid = 0, cpb = 4 * TPB, max_blocks_per_sm = 0, blocks_per_sm = 0, num_sms = 0;
   cudaGraphExec_t exec = nullptr;
   bool graph_ok = false;
-  std::vector<SolveDev> host_sv;
-  ~dg_batch() {
+
+  ~BatchCore() {
     if (stream) cudaStreamSynchronize(stream);
     if (exec) cudaGraphExecDestroy(exec);
-    for (auto *s : solves) dg_solver_destroy(s);
     cudaFree(d_sv);
     cudaFree(d_work);
     cudaFree(d_bar);
-    if (own_stream && stream) cudaStreamDestroy(stream);
+  }
+
+  int32_t init(int precision, cudaStream_t s) {
+    prec = precision;
+    stream = s;
+    int dev = 0, coop = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (!coop) return set_error(DG_EINVAL, "device does not support cooperative launches");
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&max_blocks_per_sm, kernel(), TPB, 0) != cudaSuccess ||
+        max_blocks_per_sm < 1)
+      return set_error(DG_ECUDA, "occupancy query failed");
+    blocks_per_sm = max_blocks_per_sm;
+    if (cudaMalloc(&d_bar, sizeof(BarrierState)) != cudaSuccess) return set_error(DG_ENOMEM, "barrier state");
+    BarrierState z{};
+    if (cudaMemcpy(d_bar, &z, sizeof(z), cudaMemcpyHostToDevice) != cudaSuccess) return set_error(DG_ECUDA, "barrier");
+    return DG_OK;
+  }
+
+  const void *kernel() const {
+    return prec == DG_PREC_MIXED ? (const void *)k_batch_stage<float> : (const void *)k_batch_stage<double>;
+  }
+
+  cudaError_t launch_stage(int stage) {
+    int nsv = (int)host_sv.size(), nw = nwork;
+    void *args[] = {&d_sv, &nsv, &d_work, &nw, &d_bar, &stage};
+    return cudaLaunchCooperativeKernel(kernel(), dim3(grid), dim3(TPB), args, 0, stream);
+  }
+
+  // the solves to advance (not owned); rebuilds descriptors, work list and graph
+  int32_t set_solves(const std::vector<dg_solver *> &list) {
+    if (cudaStreamSynchronize(stream) != cudaSuccess) return set_error(DG_ECUDA, "sync");
+    solves = list;
+    host_sv.clear();
+    for (dg_solver *s : solves) {
+      SolveDev d{};
+      const StageCtx &c = solver_ctx(s);
+      d.mesh = c.mesh;
+      d.ph = c.phys;
+      StateBuf un, uh, us;
+      solver_states(s, &un, &uh, &us);
+      d.avg[0] = un.avg; d.hi[0] = un.hi;
+      d.avg[1] = uh.avg; d.hi[1] = uh.hi;
+      d.avg[2] = us.avg; d.hi[2] = us.hi;
+      d.tr = c.tr; d.vd = c.vd; d.hs = c.hs;
+      d.part_sum = c.part_sum; d.part_dev = c.part_dev; d.part_alpha = c.part_alpha; d.part_cnt = c.part_cnt;
+      d.sc = c.sc;
+      d.k = c.k;
+      d.oe = c.phys.oe;
+      d.bp = c.phys.bp;
+      d.ntiles = num_blocks(c.mesh.nt);
+      host_sv.push_back(d);
+    }
+    if (host_sv.size() > sv_cap) {
+      cudaFree(d_sv);
+      d_sv = nullptr;
+      sv_cap = std::max<size_t>(host_sv.size(), 2 * sv_cap);
+      if (cudaMalloc(&d_sv, sizeof(SolveDev) * sv_cap) != cudaSuccess) { sv_cap = 0; return set_error(DG_ENOMEM, "solve table"); }
+    }
+    if (!host_sv.empty() &&
+        cudaMemcpy(d_sv, host_sv.data(), sizeof(SolveDev) * host_sv.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+      return set_error(DG_ECUDA, "solve table upload");
+    return set_shape(cpb, blocks_per_sm);
+  }
+
+  // work list of chunks of cpb cells (a multiple of TPB), then the step graph
+  int32_t set_shape(int cells_per_block, int bpsm) {
+    std::vector<WorkItem> work;
+    const int64_t tpw = cells_per_block / TPB;
+    for (size_t i = 0; i < host_sv.size(); ++i)
+      for (int64_t t = 0; t < host_sv[i].ntiles; t += tpw)
+        work.push_back(WorkItem{(int)i, 0, t, std::min<int64_t>(tpw, host_sv[i].ntiles - t)});
+    if (work.size() > work_cap) {
+      cudaFree(d_work);
+      d_work = nullptr;
+      work_cap = std::max<size_t>(work.size(), 2 * work_cap);
+      if (cudaMalloc(&d_work, sizeof(WorkItem) * work_cap) != cudaSuccess) { work_cap = 0; return set_error(DG_ENOMEM, "work list"); }
+    }
+    if (!work.empty() &&
+        cudaMemcpy(d_work, work.data(), sizeof(WorkItem) * work.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+      return set_error(DG_ECUDA, "work list upload");
+    nwork = (int)work.size();
+    cpb = cells_per_block;
+    blocks_per_sm = std::max(1, std::min(bpsm, max_blocks_per_sm));
+    grid = std::max(1, std::min(num_sms * blocks_per_sm, std::max(nwork, 1)));
+    // one SSP-RK3 step = three cooperative launches, captured as a graph when supported
+    if (exec) { cudaGraphExecDestroy(exec); exec = nullptr; }
+    graph_ok = false;
+    if (host_sv.empty()) return DG_OK;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      cudaError_t e = cudaSuccess;
+      for (int st = 0; st < 3 && e == cudaSuccess; ++st) e = launch_stage(st);
+      cudaError_t e2 = cudaStreamEndCapture(stream, &g);
+      if (e == cudaSuccess && e2 == cudaSuccess && g && cudaGraphInstantiate(&exec, g, 0) == cudaSuccess)
+        graph_ok = true;
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();   // a refused capture leaves an error behind: clear it
+    }
+    return DG_OK;
+  }
+
+  int32_t enqueue_steps(int64_t n) {
+    if (host_sv.empty()) return DG_OK;
+    for (int64_t s = 0; s < n; ++s) {
+      if (graph_ok) {
+        if (cudaGraphLaunch(exec, stream) != cudaSuccess) return set_error(DG_ECUDA, "batch graph launch");
+      } else {
+        for (int st = 0; st < 3; ++st) {
+          cudaError_t e = launch_stage(st);
+          if (e != cudaSuccess) return set_error(DG_ECUDA, cudaGetErrorString(e));
+        }
+      }
+    }
+    return DG_OK;
+  }
+
+  int32_t check_barrier() {
+    BarrierState h{};
+    if (cudaMemcpyAsync(&h, d_bar, sizeof(h), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+      return set_error(DG_ECUDA, "batch sync");
+    if (h.error) {
+      BarrierState z{};
+      cudaMemcpy(d_bar, &z, sizeof(z), cudaMemcpyHostToDevice);
+      return set_error(DG_ETIMEOUT, "a grid barrier of the batch kernel timed out");
+    }
+    return DG_OK;
   }
 };
 
-namespace {
+}  // namespace dg
 
-const void *stage_kernel(int prec) {
-  return prec == DG_PREC_MIXED ? (const void *)k_batch_stage<float> : (const void *)k_batch_stage<double>;
-}
-
-cudaError_t launch_stage(dg_batch *b, int stage) {
-  int nsv = b->n, nwork = b->nwork;
-  void *args[] = {&b->d_sv, &nsv, &b->d_work, &nwork, &b->d_bar, &stage};
-  return cudaLaunchCooperativeKernel(stage_kernel(b->prec), dim3(b->grid), dim3(TPB), args, 0, b->stream);
-}
-
-// work list of chunks of cpb cells (cpb a multiple of TPB), solve after solve
-int32_t build_work(dg_batch *b, int cpb, int blocks_per_sm) {
-  std::vector<WorkItem> work;
-  const int64_t tpw = cpb / TPB;
-  for (int i = 0; i < b->n; ++i)
-    for (int64_t t = 0; t < b->host_sv[i].ntiles; t += tpw)
-      work.push_back(WorkItem{i, 0, t, std::min<int64_t>(tpw, b->host_sv[i].ntiles - t)});
-  cudaFree(b->d_work);
-  b->d_work = nullptr;
-  if (cudaMalloc(&b->d_work, sizeof(WorkItem) * work.size()) != cudaSuccess) return set_error(DG_ENOMEM, "work list");
-  if (cudaMemcpy(b->d_work, work.data(), sizeof(WorkItem) * work.size(), cudaMemcpyHostToDevice) != cudaSuccess)
-    return set_error(DG_ECUDA, "work list upload");
-  b->nwork = (int)work.size();
-  b->cpb = cpb;
-  b->blocks_per_sm = std::max(1, std::min(blocks_per_sm, b->max_blocks_per_sm));
-  b->grid = std::max(1, std::min(b->num_sms * b->blocks_per_sm, b->nwork));
-  // one SSP-RK3 step = three cooperative launches, captured as a graph when supported
-  if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
-  b->graph_ok = false;
-  cudaGraph_t g = nullptr;
-  if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-    cudaError_t e = cudaSuccess;
-    for (int st = 0; st < 3 && e == cudaSuccess; ++st) e = launch_stage(b, st);
-    cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
-    if (e == cudaSuccess && e2 == cudaSuccess && g && cudaGraphInstantiate(&b->exec, g, 0) == cudaSuccess)
-      b->graph_ok = true;
-    if (g) cudaGraphDestroy(g);
-    cudaGetLastError();   // a refused capture leaves an error behind: clear it
+struct dg_batch {
+  BatchCore core;
+  std::vector<dg_solver *> owned;
+  bool own_stream = false;
+  cudaStream_t stream = nullptr;
+  ~dg_batch() {
+    if (stream) cudaStreamSynchronize(stream);
+    for (auto *s : owned) dg_solver_destroy(s);
+    core.~BatchCore();
+    new (&core) BatchCore();
+    if (own_stream && stream) cudaStreamDestroy(stream);
   }
-  return DG_OK;
-}
-
-int32_t enqueue_steps(dg_batch *b, int64_t n) {
-  for (int64_t s = 0; s < n; ++s) {
-    if (b->graph_ok) {
-      if (cudaGraphLaunch(b->exec, b->stream) != cudaSuccess) return set_error(DG_ECUDA, "batch graph launch");
-    } else {
-      for (int st = 0; st < 3; ++st) {
-        cudaError_t e = launch_stage(b, st);
-        if (e != cudaSuccess) return set_error(DG_ECUDA, cudaGetErrorString(e));
-      }
-    }
-  }
-  return DG_OK;
-}
-
-int32_t check_barrier(dg_batch *b) {
-  BarrierState h{};
-  if (cudaMemcpyAsync(&h, b->d_bar, sizeof(h), cudaMemcpyDeviceToHost, b->stream) != cudaSuccess ||
-      cudaStreamSynchronize(b->stream) != cudaSuccess)
-    return set_error(DG_ECUDA, "batch sync");
-  if (h.error) {
-    BarrierState z{};
-    cudaMemcpy(b->d_bar, &z, sizeof(z), cudaMemcpyHostToDevice);
-    return set_error(DG_ETIMEOUT, "a grid barrier of the batch kernel timed out");
-  }
-  return DG_OK;
-}
-
-}  // namespace
+};
 
 extern "C" int32_t dg_batch_create(int32_t n, const dg_mesh *const *meshes, const dg_config *cfgs,
                                    const double *const *coeffs, void *cuda_stream, dg_batch **out) {
@@ -266,8 +343,6 @@ extern "C" int32_t dg_batch_create(int32_t n, const dg_mesh *const *meshes, cons
     if (cfgs[i].precision != cfgs[0].precision) return set_error(DG_EINVAL, "a batch has one precision");
   auto b = new (std::nothrow) dg_batch();
   if (!b) return set_error(DG_ENOMEM, "host allocation failed");
-  b->n = n;
-  b->prec = cfgs[0].precision;
   if (cuda_stream) {
     b->stream = (cudaStream_t)cuda_stream;
   } else {
@@ -277,48 +352,13 @@ extern "C" int32_t dg_batch_create(int32_t n, const dg_mesh *const *meshes, cons
     }
     b->own_stream = true;
   }
-  for (int i = 0; i < n; ++i) {
+  int32_t rc = b->core.init(cfgs[0].precision, b->stream);
+  for (int i = 0; i < n && rc == DG_OK; ++i) {
     dg_solver *s = nullptr;
-    int32_t rc = dg_init(meshes[i], &cfgs[i], coeffs[i], b->stream, &s);
-    if (rc != DG_OK) { delete b; return rc; }
-    b->solves.push_back(s);
-    SolveDev d{};
-    const StageCtx &c = solver_ctx(s);
-    d.mesh = c.mesh;
-    d.ph = c.phys;
-    StateBuf un, uh, us;
-    solver_states(s, &un, &uh, &us);
-    d.avg[0] = un.avg; d.hi[0] = un.hi;
-    d.avg[1] = uh.avg; d.hi[1] = uh.hi;
-    d.avg[2] = us.avg; d.hi[2] = us.hi;
-    d.tr = c.tr; d.vd = c.vd; d.hs = c.hs;
-    d.part_sum = c.part_sum; d.part_dev = c.part_dev; d.part_alpha = c.part_alpha; d.part_cnt = c.part_cnt;
-    d.sc = c.sc;
-    d.k = cfgs[i].k;
-    d.oe = cfgs[i].oe;
-    d.bp = cfgs[i].bp;
-    d.ntiles = num_blocks(c.mesh.nt);
-    b->host_sv.push_back(d);
+    rc = dg_init(meshes[i], &cfgs[i], coeffs[i], b->stream, &s);
+    if (rc == DG_OK) b->owned.push_back(s);
   }
-  int dev = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev);
-  int coop = 0;
-  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-  if (!coop) { delete b; return set_error(DG_EINVAL, "device does not support cooperative launches"); }
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->max_blocks_per_sm, stage_kernel(b->prec), TPB, 0) !=
-          cudaSuccess || b->max_blocks_per_sm < 1) {
-    delete b;
-    return set_error(DG_ECUDA, "occupancy query failed");
-  }
-  if (cudaMalloc(&b->d_sv, sizeof(SolveDev) * n) != cudaSuccess || cudaMalloc(&b->d_bar, sizeof(BarrierState)) != cudaSuccess) {
-    delete b;
-    return set_error(DG_ENOMEM, "batch descriptors");
-  }
-  BarrierState z{};
-  cudaMemcpy(b->d_sv, b->host_sv.data(), sizeof(SolveDev) * n, cudaMemcpyHostToDevice);
-  cudaMemcpy(b->d_bar, &z, sizeof(z), cudaMemcpyHostToDevice);
-  int32_t rc = build_work(b, 4 * TPB, b->max_blocks_per_sm);
+  if (rc == DG_OK) rc = b->core.set_solves(b->owned);
   if (rc != DG_OK) { delete b; return rc; }
   *out = b;
   return DG_OK;
@@ -330,57 +370,59 @@ extern "C" int32_t dg_batch_set_shape(dg_batch *b, int32_t cells_per_block, int3
   if (!b || cells_per_block < TPB || cells_per_block % TPB != 0 || blocks_per_sm < 1)
     return set_error(DG_EINVAL, "cells_per_block must be a positive multiple of 128, blocks_per_sm >= 1");
   if (cudaStreamSynchronize(b->stream) != cudaSuccess) return set_error(DG_ECUDA, "sync");
-  return build_work(b, cells_per_block, blocks_per_sm);
+  return b->core.set_shape(cells_per_block, blocks_per_sm);
 }
 
 extern "C" int32_t dg_batch_shape(const dg_batch *b, int32_t *cells_per_block, int32_t *blocks_per_sm,
                                   int32_t *grid, int32_t *graph) {
   if (!b) return set_error(DG_EINVAL, "batch is NULL");
-  if (cells_per_block) *cells_per_block = b->cpb;
-  if (blocks_per_sm) *blocks_per_sm = b->blocks_per_sm;
-  if (grid) *grid = b->grid;
-  if (graph) *graph = b->graph_ok ? 1 : 0;
+  if (cells_per_block) *cells_per_block = b->core.cpb;
+  if (blocks_per_sm) *blocks_per_sm = b->core.blocks_per_sm;
+  if (grid) *grid = b->core.grid;
+  if (graph) *graph = b->core.graph_ok ? 1 : 0;
   return DG_OK;
 }
 
 extern "C" int32_t dg_batch_advance_async(dg_batch *b, int64_t nsteps) {
   if (!b || nsteps < 0) return set_error(DG_EINVAL, "bad argument");
-  return enqueue_steps(b, nsteps);
+  return b->core.enqueue_steps(nsteps);
 }
 
-extern "C" int32_t dg_batch_advance(dg_batch *b, const double *t_end, int64_t max_steps, dg_stats *stats) {
-  if (!b || max_steps < 0) return set_error(DG_EINVAL, "bad argument");
-  std::vector<Scalars> h(b->n), start(b->n);
-  for (int i = 0; i < b->n; ++i) {
-    if (cudaMemcpyAsync(&h[i], b->host_sv[i].sc, sizeof(Scalars), cudaMemcpyDeviceToHost, b->stream) != cudaSuccess)
+namespace dg {
+// advance the solves of a batch core until every one reached its t_end (or max_steps)
+int32_t batch_advance(BatchCore &core, const double *t_end, int64_t max_steps, dg_stats *stats) {
+  const size_t n = core.solves.size();
+  std::vector<Scalars> h(n), start(n);
+  for (size_t i = 0; i < n; ++i) {
+    if (cudaMemcpyAsync(&h[i], core.host_sv[i].sc, sizeof(Scalars), cudaMemcpyDeviceToHost, core.stream) != cudaSuccess)
       return set_error(DG_ECUDA, "scalars");
   }
-  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return set_error(DG_ECUDA, "sync");
+  if (cudaStreamSynchronize(core.stream) != cudaSuccess) return set_error(DG_ECUDA, "sync");
   start = h;
-  for (int i = 0; i < b->n; ++i) {
+  for (size_t i = 0; i < n; ++i) {
     h[i].t_end = t_end ? t_end[i] : INFINITY;
-    if (cudaMemcpyAsync(&b->host_sv[i].sc->t_end, &h[i].t_end, sizeof(double), cudaMemcpyHostToDevice, b->stream) !=
-        cudaSuccess)
+    if (cudaMemcpyAsync(&core.host_sv[i].sc->t_end, &h[i].t_end, sizeof(double), cudaMemcpyHostToDevice,
+                        core.stream) != cudaSuccess)
       return set_error(DG_ECUDA, "t_end");
   }
   int64_t done = 0;
   auto unfinished = [&]() {
-    for (int i = 0; i < b->n; ++i)
+    for (size_t i = 0; i < n; ++i)
       if (h[i].t < h[i].t_end && std::isfinite(h[i].alpha) && h[i].alpha > 0.0) return true;
     return false;
   };
   while (done < max_steps && unfinished()) {
     const int64_t chunk = std::min<int64_t>(max_steps - done, 32);
-    int32_t rc = enqueue_steps(b, chunk);
+    int32_t rc = core.enqueue_steps(chunk);
     if (rc != DG_OK) return rc;
     done += chunk;
-    if ((rc = check_barrier(b)) != DG_OK) return rc;
-    for (int i = 0; i < b->n; ++i)
-      cudaMemcpyAsync(&h[i], b->host_sv[i].sc, sizeof(Scalars), cudaMemcpyDeviceToHost, b->stream);
-    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return set_error(DG_ECUDA, "sync");
+    if ((rc = core.check_barrier()) != DG_OK) return rc;
+    for (size_t i = 0; i < n; ++i)
+      cudaMemcpyAsync(&h[i], core.host_sv[i].sc, sizeof(Scalars), cudaMemcpyDeviceToHost, core.stream);
+    if (cudaStreamSynchronize(core.stream) != cudaSuccess) return set_error(DG_ECUDA, "sync");
   }
   int64_t bad = 0;
-  for (int i = 0; i < b->n; ++i) {
+  for (size_t i = 0; i < n; ++i) {
     if (stats) {
       stats[i].steps = h[i].steps - start[i].steps;
       stats[i].limited_cells = h[i].limited - start[i].limited;
@@ -395,29 +437,37 @@ extern "C" int32_t dg_batch_advance(dg_batch *b, const double *t_end, int64_t ma
   if (bad > 0) return set_error(DG_ENONPHYS, "cell averages left the admissible set in the batch");
   return DG_OK;
 }
+}  // namespace dg
+
+extern "C" int32_t dg_batch_advance(dg_batch *b, const double *t_end, int64_t max_steps, dg_stats *stats) {
+  if (!b || max_steps < 0) return set_error(DG_EINVAL, "bad argument");
+  return batch_advance(b->core, t_end, max_steps, stats);
+}
 
 extern "C" int32_t dg_batch_sync(dg_batch *b) {
   if (!b) return set_error(DG_EINVAL, "batch is NULL");
-  return check_barrier(b);
+  return b->core.check_barrier();
 }
 
 extern "C" int32_t dg_batch_solver(dg_batch *b, int32_t i, dg_solver **out) {
-  if (!b || !out || i < 0 || i >= b->n) return set_error(DG_EINVAL, "bad index");
-  *out = b->solves[i];
+  if (!b || !out || i < 0 || i >= (int32_t)b->owned.size()) return set_error(DG_EINVAL, "bad index");
+  *out = b->owned[i];
   return DG_OK;
 }
 
 extern "C" int32_t dg_batch_autotune(dg_batch *b, int32_t steps, int32_t *best_cpb, int32_t *best_bpsm,
                                      double *best_ms) {
   if (!b || steps < 1) return set_error(DG_EINVAL, "bad argument");
+  BatchCore &core = b->core;
+  const int n = (int)core.solves.size();
   // snapshot every solve's device state (averages, modes, traces of u_n and
   // scalars); restoring these bytes undoes the tuning steps exactly
   struct Snap { void *avg, *hi, *tr; size_t navg, nhi, ntr; Scalars sc; };
-  std::vector<Snap> snaps(b->n);
-  const size_t rs = b->prec == DG_PREC_MIXED ? sizeof(float) : sizeof(double);
+  std::vector<Snap> snaps(n);
+  const size_t rs = core.prec == DG_PREC_MIXED ? sizeof(float) : sizeof(double);
   auto free_snaps = [&]() { for (auto &q : snaps) { cudaFree(q.avg); cudaFree(q.hi); cudaFree(q.tr); } };
-  for (int i = 0; i < b->n; ++i) {
-    dg_solver *s = b->solves[i];
+  for (int i = 0; i < n; ++i) {
+    dg_solver *s = core.solves[i];
     const int64_t nt = solver_ctx(s).mesh.nt;
     const int nb = solver_nb(s), nq = nb == 3 ? 2 : 3;
     StateBuf un, uh, us;
@@ -429,25 +479,25 @@ extern "C" int32_t dg_batch_autotune(dg_batch *b, int32_t steps, int32_t *best_c
       free_snaps();
       return set_error(DG_ENOMEM, "autotune snapshot");
     }
-    cudaMemcpyAsync(q.avg, un.avg, q.navg, cudaMemcpyDeviceToDevice, b->stream);
-    cudaMemcpyAsync(q.hi, un.hi, q.nhi, cudaMemcpyDeviceToDevice, b->stream);
-    cudaMemcpyAsync(q.tr, solver_ctx(s).tr, q.ntr, cudaMemcpyDeviceToDevice, b->stream);
+    cudaMemcpyAsync(q.avg, un.avg, q.navg, cudaMemcpyDeviceToDevice, core.stream);
+    cudaMemcpyAsync(q.hi, un.hi, q.nhi, cudaMemcpyDeviceToDevice, core.stream);
+    cudaMemcpyAsync(q.tr, solver_ctx(s).tr, q.ntr, cudaMemcpyDeviceToDevice, core.stream);
     if (solver_read_scalars(s, &q.sc) != DG_OK) { free_snaps(); return DG_ECUDA; }
   }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   double best = INFINITY;
-  int bc = b->cpb, bb = b->blocks_per_sm;
+  int bc = core.cpb, bb = core.blocks_per_sm;
   const int cpbs[4] = {TPB, 2 * TPB, 4 * TPB, 8 * TPB};
   for (int ci = 0; ci < 4; ++ci)
-    for (int bpsm = 1; bpsm <= b->max_blocks_per_sm; ++bpsm) {
-      int32_t rc = build_work(b, cpbs[ci], bpsm);
-      if (rc == DG_OK) rc = enqueue_steps(b, 1);   // warm-up
-      cudaEventRecord(e0, b->stream);
-      if (rc == DG_OK) rc = enqueue_steps(b, steps);
-      cudaEventRecord(e1, b->stream);
-      if (rc == DG_OK) rc = check_barrier(b);
+    for (int bpsm = 1; bpsm <= core.max_blocks_per_sm; ++bpsm) {
+      int32_t rc = core.set_shape(cpbs[ci], bpsm);
+      if (rc == DG_OK) rc = core.enqueue_steps(1);   // warm-up
+      cudaEventRecord(e0, core.stream);
+      if (rc == DG_OK) rc = core.enqueue_steps(steps);
+      cudaEventRecord(e1, core.stream);
+      if (rc == DG_OK) rc = core.check_barrier();
       if (rc != DG_OK) { free_snaps(); return rc; }
       float ms = 0.0f;
       cudaEventElapsedTime(&ms, e0, e1);
@@ -455,21 +505,41 @@ extern "C" int32_t dg_batch_autotune(dg_batch *b, int32_t steps, int32_t *best_c
     }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  for (int i = 0; i < b->n; ++i) {
-    dg_solver *s = b->solves[i];
+  for (int i = 0; i < n; ++i) {
+    dg_solver *s = core.solves[i];
     StateBuf un, uh, us;
     solver_states(s, &un, &uh, &us);
     const Snap &q = snaps[i];
-    cudaMemcpyAsync(un.avg, q.avg, q.navg, cudaMemcpyDeviceToDevice, b->stream);
-    cudaMemcpyAsync(un.hi, q.hi, q.nhi, cudaMemcpyDeviceToDevice, b->stream);
-    cudaMemcpyAsync(solver_ctx(s).tr, q.tr, q.ntr, cudaMemcpyDeviceToDevice, b->stream);
+    cudaMemcpyAsync(un.avg, q.avg, q.navg, cudaMemcpyDeviceToDevice, core.stream);
+    cudaMemcpyAsync(un.hi, q.hi, q.nhi, cudaMemcpyDeviceToDevice, core.stream);
+    cudaMemcpyAsync(solver_ctx(s).tr, q.tr, q.ntr, cudaMemcpyDeviceToDevice, core.stream);
     if (solver_write_scalars(s, &q.sc) != DG_OK) { free_snaps(); return DG_ECUDA; }
   }
   free_snaps();
-  int32_t rc = build_work(b, bc, bb);
+  int32_t rc = core.set_shape(bc, bb);
   if (rc != DG_OK) return rc;
   if (best_cpb) *best_cpb = bc;
   if (best_bpsm) *best_bpsm = bb;
   if (best_ms) *best_ms = best / steps;
   return DG_OK;
 }
+
+// ============================================================================
+// Batch core for the server (dg_serve.cu)
+// ============================================================================
+namespace dg {
+int32_t batch_core_new(int precision, cudaStream_t stream, BatchCore **out) {
+  auto c = new (std::nothrow) BatchCore();
+  if (!c) return set_error(DG_ENOMEM, "host allocation failed");
+  int32_t rc = c->init(precision, stream);
+  if (rc != DG_OK) { delete c; return rc; }
+  *out = c;
+  return DG_OK;
+}
+void batch_core_delete(BatchCore *core) { delete core; }
+int32_t batch_core_set_solves(BatchCore *core, const std::vector<dg_solver *> &list) {
+  return core->set_solves(list);
+}
+int32_t batch_core_enqueue(BatchCore *core, int64_t nsteps) { return core->enqueue_steps(nsteps); }
+int32_t batch_core_check(BatchCore *core) { return core->check_barrier(); }
+}  // namespace dg

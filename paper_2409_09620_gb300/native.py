@@ -77,6 +77,13 @@ SIGNATURES = {
     "dg_batch_set_shape": (i32, [P, i32, i32]),
     "dg_batch_shape": (i32, [P, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
     "dg_batch_autotune": (i32, [P, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(dbl)]),
+    "dg_server_create": (i32, [i32, C.c_size_t, i32, P, C.POINTER(P)]),
+    "dg_server_destroy": (None, [P]),
+    "dg_server_submit": (i32, [P, i64, P, i64, P, P, P, P, P, dbl, C.POINTER(i64)]),
+    "dg_server_tick": (i32, [P, C.POINTER(i32), C.POINTER(i32)]),
+    "dg_server_request": (i32, [P, i64, P]),
+    "dg_server_result": (i32, [P, i64, P, C.c_size_t]),
+    "dg_server_stats": (i32, [P, C.POINTER(i64), C.POINTER(i64)]),
     "dg_last_error": (C.c_char_p, []),
 }
 
@@ -361,6 +368,73 @@ class Batch:
         a, b, ms = i32(), i32(), dbl()
         _check(lib().dg_batch_autotune(self.h, steps, C.byref(a), C.byref(b), C.byref(ms)))
         return dict(cells_per_block=a.value, blocks_per_sm=b.value, ms_per_step=ms.value)
+
+
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
+
+
+class RequestInfo(C.Structure):
+    _fields_ = [("state", i32), ("error", i32), ("cells", i64), ("steps", i64), ("t", dbl), ("t_end", dbl),
+                ("submit_s", dbl), ("start_s", dbl), ("done_s", dbl), ("device_bytes", i64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Server:
+    """dg_server handle: continuous batching of solve requests."""
+
+    def __init__(self, precision=PREC_FP64, budget_bytes=8 << 30, steps_per_tick=8, stream=None):
+        h = P()
+        _check(lib().dg_server_create(precision, budget_bytes, steps_per_tick,
+                                      None if stream is None else P(stream), C.byref(h)))
+        self.h = h
+        self._nb = {}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().dg_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, mesh, cfg, coeffs, t_end):
+        """mesh: a workloads.Mesh (host arrays); returns the request id."""
+        xy = np.ascontiguousarray(mesh.xy, np.float64)
+        tri = np.ascontiguousarray(mesh.tri, np.int32)
+        canon = np.ascontiguousarray(mesh.canon, np.int32)
+        bc = np.ascontiguousarray(mesh.bc, np.int8)
+        u = np.ascontiguousarray(coeffs, np.float64)
+        rid = i64()
+        _check(lib().dg_server_submit(self.h, xy.shape[0], _p(xy), tri.shape[0], _p(tri), _p(canon), _p(bc),
+                                      C.byref(cfg), _p(u), t_end, C.byref(rid)))
+        self._nb[rid.value] = (u.shape, tri.shape[0])
+        return rid.value
+
+    def tick(self):
+        r, q = i32(), i32()
+        _check(lib().dg_server_tick(self.h, C.byref(r), C.byref(q)))
+        return r.value, q.value
+
+    def info(self, rid):
+        inf = RequestInfo()
+        _check(lib().dg_server_request(self.h, rid, C.byref(inf)))
+        return inf.as_dict()
+
+    def result(self, rid):
+        shape, _ = self._nb[rid]
+        out = np.empty(shape)
+        _check(lib().dg_server_result(self.h, rid, _p(out), out.size))
+        return out
+
+    def stats(self):
+        a, b = i64(), i64()
+        _check(lib().dg_server_stats(self.h, C.byref(a), C.byref(b)))
+        return dict(bytes_in_use=a.value, cell_stages_done=b.value)
 
 
 def initial_state(mesh: Mesh, workload):

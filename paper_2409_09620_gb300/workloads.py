@@ -325,3 +325,27 @@ def batch_workloads(n=64, seed=7, cmin=2000, cmax=200000):
         side = max(4, int(round(math.sqrt(cells / 2.0))))
         out.append(riemann4_workload(n=side, k=k, seed=seed * 1000 + i))
     return out
+
+
+def serving_requests(n=24, seed=11, rate=30.0, cmin=1000, cmax=100000, t_end=(0.005, 0.02)):
+    """Seeded solve requests of the serving benchmark: Poisson arrivals at
+    `rate` per second, cells log-uniform in [cmin, cmax], P1 or P2, initial data
+    drawn from the isentropic vortex, the Sedov-type blast and the four-quadrant
+    Riemann problem, end time uniform in t_end.  Returns (workload, t_end,
+    arrival offset in s) triples."""
+    rng = np.random.default_rng(seed)
+    out, at = [], 0.0
+    for i in range(n):
+        at += rng.exponential(1.0 / rate)
+        k = int(rng.integers(1, 3))
+        cells = math.exp(rng.uniform(math.log(cmin), math.log(cmax)))
+        side = max(4, int(round(math.sqrt(cells / 2.0))))
+        kind = int(rng.integers(0, 3))
+        if kind == 0:
+            wl = vortex_workload(n=side, k=k, seed=seed * 100 + i)
+        elif kind == 1:
+            wl = sedov_workload(n=side + (side % 2), k=k, seed=seed * 100 + i)
+        else:
+            wl = riemann4_workload(n=side, k=k, seed=seed * 100 + i)
+        out.append((wl, float(rng.uniform(*t_end)), at))
+    return out
