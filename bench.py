@@ -45,9 +45,9 @@ ALGO_FLOPS_P2 = {"rk": 2110.0, "stats": 270.0, "oe_bp": 1615.0}
 # (2 DFMA + DADD + DMUL per launch from one ncu capture / cells); division,
 # square root and exp expand into DFMA sequences.  None = not re-measured since
 # the kernel last changed.
-EXECUTED_FLOPS_P2 = {"oe_bp": None}
+EXECUTED_FLOPS_P2 = {"rk": 2116.0, "oe_bp": None, "stats": None}
 # DRAM bytes per launch of the dominant kernel from the same ncu capture.
-TRAFFIC_PER_LAUNCH = {"oe_bp": None}
+TRAFFIC_PER_LAUNCH = {"rk": 1.532e9, "oe_bp": None, "stats": None}
 
 
 def load_peaks():
@@ -222,6 +222,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=10)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                    help="precision of the primary timed run")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=10)
     ap.add_argument("--no-serving", action="store_true")
@@ -271,7 +273,8 @@ def main():
         prof = solver.profile_steps(args.profile_steps) if args.profile_steps > 0 else None
         return solver, ms, st, clocks, prof
 
-    solver, ms, st, clocks, prof = timed(N.PREC_FP64)
+    primary = N.PREC_FP64 if args.precision == "fp64" else N.PREC_MIXED
+    solver, ms, st, clocks, prof = timed(primary)
     ms_max = dist_max(ms, world)
     value = nt * 3 * args.steps * world / (ms_max / 1e3)
 

@@ -55,11 +55,15 @@ struct dg_mesh {
          *c_area = nullptr, *hgeo = nullptr;
   int8_t *limv = nullptr;
   int32_t *conn = nullptr;
+  int64_t ne = 0;
+  int32_t *e_cell = nullptr, *etile = nullptr, *cedge = nullptr;
+  int8_t *e_loc = nullptr;
   double min_ca[4] = {0, 0, 0, 0};   // (P1 optimal, P1 ZXS, P2 optimal, P2 ZXS)
   double area_total = 0.0;
   ~dg_mesh() {
     cudaFree(area); cudaFree(jinv); cudaFree(nrm); cudaFree(len); cudaFree(vxy); cudaFree(node);
     cudaFree(c_area); cudaFree(limv); cudaFree(conn); cudaFree(hgeo);
+    cudaFree(e_cell); cudaFree(e_loc); cudaFree(etile); cudaFree(cedge);
   }
 };
 
@@ -70,7 +74,7 @@ struct dg_solver {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   StateBuf un{}, uh{}, us{};
-  void *tr = nullptr, *vd = nullptr, *hs = nullptr;
+  void *tr = nullptr, *vd = nullptr, *hs = nullptr, *ej = nullptr;
   double *part_sum = nullptr, *part_dev = nullptr, *part_alpha = nullptr;
   long long *part_cnt = nullptr;
   Scalars *sc = nullptr;
@@ -80,7 +84,7 @@ struct dg_solver {
     if (step_exec) cudaGraphExecDestroy(step_exec);
     StateBuf *bufs[3] = {&un, &uh, &us};
     for (auto *b : bufs) { cudaFree(b->avg); cudaFree(b->hi); }
-    cudaFree(tr); cudaFree(vd); cudaFree(hs);
+    cudaFree(tr); cudaFree(vd); cudaFree(hs); cudaFree(ej);
     cudaFree(part_sum); cudaFree(part_dev); cudaFree(part_alpha); cudaFree(part_cnt); cudaFree(sc);
     if (own_stream && stream) cudaStreamDestroy(stream);
   }
@@ -176,6 +180,29 @@ extern "C" int32_t dg_mesh_create(int64_t nv, const double *xy, int64_t nt, cons
       const int32_t nbK = m->nbr[3 * K + i];
       conn[(size_t)i * nt + K] = nbK >= 0 ? ((nbK << 2) | m->nbr_edge[3 * K + i]) : -(int32_t)bc[3 * K + i];
     }
+  // edge list: every edge once, owned by its lower cell id (or its only cell),
+  // ordered by owner; tiles of TPB cells own contiguous edge ranges
+  const int64_t ntiles = num_blocks(nt);
+  std::vector<int32_t> e_cell, etile((size_t)ntiles + 1), cedge((size_t)(3 * nt));
+  std::vector<int8_t> e_loc;
+  for (int64_t K = 0; K < nt; ++K) {
+    if (K % TPB == 0) etile[(size_t)(K / TPB)] = (int32_t)e_cell.size();
+    for (int i = 0; i < 3; ++i) {
+      const int32_t nbK = m->nbr[3 * K + i];
+      if (nbK < 0 || K < nbK) {
+        cedge[(size_t)i * nt + K] = (int32_t)e_cell.size();
+        e_cell.push_back((int32_t)K);
+        e_loc.push_back((int8_t)i);
+      }
+    }
+  }
+  etile[(size_t)ntiles] = (int32_t)e_cell.size();
+  for (int64_t K = 0; K < nt; ++K)
+    for (int i = 0; i < 3; ++i) {
+      const int32_t nbK = m->nbr[3 * K + i];
+      if (nbK >= 0 && nbK < K) cedge[(size_t)i * nt + K] = cedge[(size_t)m->nbr_edge[3 * K + i] * nt + nbK];
+    }
+  m->ne = (int64_t)e_cell.size();
   m->vxy_host.resize((size_t)(6 * nt));
   for (int64_t K = 0; K < nt; ++K)
     for (int v = 0; v < 3; ++v) {
@@ -199,6 +226,14 @@ extern "C" int32_t dg_mesh_create(int64_t nv, const double *xy, int64_t nt, cons
   MTRY(dalloc(&m->c_area, 4 * nt));
   MTRY(dalloc(&m->limv, 2 * nt));
   MTRY(dalloc(&m->conn, 3 * nt));
+  MTRY(dalloc(&m->e_cell, m->ne));
+  MTRY(dalloc(&m->e_loc, m->ne));
+  MTRY(dalloc(&m->etile, ntiles + 1));
+  MTRY(dalloc(&m->cedge, 3 * nt));
+  MTRY(cudaMemcpy(m->e_cell, e_cell.data(), sizeof(int32_t) * m->ne, cudaMemcpyHostToDevice));
+  MTRY(cudaMemcpy(m->e_loc, e_loc.data(), m->ne, cudaMemcpyHostToDevice));
+  MTRY(cudaMemcpy(m->etile, etile.data(), sizeof(int32_t) * (ntiles + 1), cudaMemcpyHostToDevice));
+  MTRY(cudaMemcpy(m->cedge, cedge.data(), sizeof(int32_t) * 3 * nt, cudaMemcpyHostToDevice));
   MTRY(dalloc(&part, 4 * num_blocks(nt)));
   MTRY(dalloc(&mins, 4));
   MTRY(cudaMemcpy(m->vxy, m->vxy_host.data(), sizeof(double) * 6 * nt, cudaMemcpyHostToDevice));
@@ -400,7 +435,7 @@ void enqueue_step(dg_solver *s) {
   for (int st = 0; st < 3; ++st) {
     const StateBuf &v = st == 0 ? s->un : s->us;
     launch_rk(c, v, s->un, s->uh, RK_A[st], RK_B[st], C_IN[st]);
-    if (oe) launch_stats(c, s->uh);
+    if (oe) launch_stats(c, s->uh, C_OUT[st]);
     launch_oe_bp(c, s->uh, st == 2 ? s->un : s->us, oe, bp, C_OUT[st], st);
   }
 }
@@ -448,6 +483,7 @@ extern "C" int32_t dg_init(const dg_mesh *mesh, const dg_config *cfg, const doub
   STRY(cudaMalloc(&s->tr, rs * nt * 3 * nq * 8));
   STRY(cudaMalloc(&s->vd, rs * nt * 42));
   STRY(cudaMalloc(&s->hs, rs * nt * 12));
+  STRY(cudaMalloc(&s->ej, rs * std::max<int64_t>(mesh->ne, 1) * EJ_ROWS));
   STRY(dalloc(&s->part_sum, 4 * nblk));
   STRY(dalloc(&s->part_dev, 5 * nblk));
   STRY(dalloc(&s->part_alpha, nblk));
@@ -458,8 +494,9 @@ extern "C" int32_t dg_init(const dg_mesh *mesh, const dg_config *cfg, const doub
   c.stream = s->stream;
   c.k = cfg->k;
   c.prec = cfg->precision;
-  c.mesh = MeshDev{nt,         mesh->area, mesh->jinv, mesh->nrm, mesh->len, mesh->vxy,
-                   mesh->node, mesh->hgeo, mesh->limv, mesh->conn};
+  c.mesh = MeshDev{nt,         mesh->area, mesh->jinv,   mesh->nrm,   mesh->len,   mesh->vxy,  mesh->node,
+                   mesh->hgeo, mesh->limv, mesh->conn,   mesh->ne,    mesh->e_cell, mesh->e_loc, mesh->etile,
+                   mesh->cedge};
   Phys &ph = c.phys;
   std::memset(&ph, 0, sizeof(ph));
   ph.gamma = cfg->gamma;
@@ -478,6 +515,7 @@ extern "C" int32_t dg_init(const dg_mesh *mesh, const dg_config *cfg, const doub
   c.tr = s->tr;
   c.vd = s->vd;
   c.hs = s->hs;
+  c.ej = s->ej;
   c.part_sum = s->part_sum;
   c.part_dev = s->part_dev;
   c.part_alpha = s->part_alpha;
@@ -632,7 +670,7 @@ extern "C" int32_t dg_profile_steps(dg_solver *s, int64_t n, double *ms, int64_t
       rec(1, [&] { launch_rk_only(c, v, s->un, s->uh, RK_A[st], RK_B[st], C_IN[st]); });
       rec(2, [&] { launch_fin_mean(c); });
       if (oe) {
-        rec(3, [&] { launch_stats_only(c, s->uh); });
+        rec(3, [&] { launch_stats_only(c, s->uh, C_OUT[st]); });
         rec(4, [&] { launch_fin_dev(c); });
       }
       rec(5, [&] { launch_oe_bp_only(c, s->uh, st == 2 ? s->un : s->us, oe, bp, C_OUT[st]); });
@@ -689,7 +727,7 @@ extern "C" int32_t dg_op_stats(dg_solver *s, const double *u, double *stats) {
   launch_oe_bp(s->ctx, s->us, s->un, 0, 0, 0.0, -1);
   if ((rc = write_scalars(s, &h)) != DG_OK) return rc;
   launch_rk(s->ctx, s->un, s->un, s->uh, 1.0, 0.0, 0.0);   // uh = u, with |K| u^(0) block sums
-  launch_stats(s->ctx, s->uh);
+  launch_stats(s->ctx, s->uh, 0.0);
   CUDA_TRY(cudaGetLastError());
   if ((rc = read_scalars(s, &h)) != DG_OK) return rc;
   for (int c = 0; c < 4; ++c) stats[c] = h.mean[c];
@@ -711,6 +749,12 @@ extern "C" int32_t dg_op_oe(dg_solver *s, const double *u, double dt, const doub
   launch_oe_bp(s->ctx, s->us, s->un, 0, 0, 0.0, -1);
   if ((rc = write_scalars(s, &h)) != DG_OK) return rc;
   launch_rk(s->ctx, s->un, s->un, s->uh, 1.0, 0.0, 0.0);   // vertex derivatives of u
+  CUDA_TRY(cudaGetLastError());
+  if ((rc = read_scalars(s, &h)) != DG_OK) return rc;
+  h.t = t;
+  h.dt = dt;
+  if ((rc = write_scalars(s, &h)) != DG_OK) return rc;
+  launch_stats_only(s->ctx, s->uh, 0.0);                    // jump data of every edge at time t
   CUDA_TRY(cudaGetLastError());
   if ((rc = read_scalars(s, &h)) != DG_OK) return rc;
   for (int c = 0; c < 4; ++c) h.mean[c] = stats[c];

@@ -24,7 +24,7 @@ struct SolveDev {
   Phys ph;
   double *avg[3];   // u_n, u_h, u_s
   void *hi[3];
-  void *tr, *vd, *hs;
+  void *tr, *vd, *hs, *ej;
   double *part_sum, *part_dev, *part_alpha;
   long long *part_cnt;
   Scalars *sc;
@@ -128,8 +128,13 @@ __global__ void __launch_bounds__(TPB) k_batch_stage(const SolveDev *__restrict_
     if (!S.sc->active || !S.oe) continue;
     const StateDev<Real> uh{S.avg[1], (Real *)S.hi[1]};
     for (int64_t t = it.first_tile; t < it.first_tile + it.ntiles; ++t) {
-      if (S.k == 1) stats_tile<1, Real>(S.mesh, uh, S.part_dev, S.sc, t);
-      else stats_tile<2, Real>(S.mesh, uh, S.part_dev, S.sc, t);
+      if (S.k == 1) {
+        stats_tile<1, Real>(S.mesh, uh, S.part_dev, S.sc, t);
+        edge_tile<1, Real>(S.mesh, S.ph, (const Real *)S.vd, (const Real *)S.hs, (Real *)S.ej, S.sc, c_out, t);
+      } else {
+        stats_tile<2, Real>(S.mesh, uh, S.part_dev, S.sc, t);
+        edge_tile<2, Real>(S.mesh, S.ph, (const Real *)S.vd, (const Real *)S.hs, (Real *)S.ej, S.sc, c_out, t);
+      }
     }
   }
   if (!grid_sync(bar, nb)) return;
@@ -144,11 +149,11 @@ __global__ void __launch_bounds__(TPB) k_batch_stage(const SolveDev *__restrict_
     const StateDev<Real> uh{S.avg[1], (Real *)S.hi[1]}, out{S.avg[oi], (Real *)S.hi[oi]};
     for (int64_t t = it.first_tile; t < it.first_tile + it.ntiles; ++t) {
       if (S.k == 1)
-        oe_bp_tile<1, Real>(S.mesh, S.ph, uh, out, (const Real *)S.vd, (const Real *)S.hs, (Real *)S.tr,
-                            S.part_alpha, S.part_cnt, S.sc, S.oe != 0, S.bp != 0, c_out, t);
+        oe_bp_tile<1, Real>(S.mesh, S.ph, uh, out, (const Real *)S.ej, (Real *)S.tr, S.part_alpha, S.part_cnt,
+                            S.sc, S.oe != 0, S.bp != 0, c_out, t);
       else
-        oe_bp_tile<2, Real>(S.mesh, S.ph, uh, out, (const Real *)S.vd, (const Real *)S.hs, (Real *)S.tr,
-                            S.part_alpha, S.part_cnt, S.sc, S.oe != 0, S.bp != 0, c_out, t);
+        oe_bp_tile<2, Real>(S.mesh, S.ph, uh, out, (const Real *)S.ej, (Real *)S.tr, S.part_alpha, S.part_cnt,
+                            S.sc, S.oe != 0, S.bp != 0, c_out, t);
     }
   }
   if (!grid_sync(bar, nb)) return;
@@ -231,7 +236,7 @@ struct BatchCore {
       d.avg[0] = un.avg; d.hi[0] = un.hi;
       d.avg[1] = uh.avg; d.hi[1] = uh.hi;
       d.avg[2] = us.avg; d.hi[2] = us.hi;
-      d.tr = c.tr; d.vd = c.vd; d.hs = c.hs;
+      d.tr = c.tr; d.vd = c.vd; d.hs = c.hs; d.ej = c.ej;
       d.part_sum = c.part_sum; d.part_dev = c.part_dev; d.part_alpha = c.part_alpha; d.part_cnt = c.part_cnt;
       d.sc = c.sc;
       d.k = c.k;

@@ -12,6 +12,7 @@
 //             vd[nt][3][14]    value (4), physical gradient (8), 1/rho and sound speed
 //                              of u_h at each vertex
 //             hs[nt][12]       physical Hessian (xx, xy, yy) of u_h per component (P2)
+//             ej[13][ne]       per edge: beta and the square roots of the OE jump sums
 // Every kernel is one thread per cell; reductions are per-block partials
 // reduced in a fixed order, so results are bitwise reproducible.
 #pragma once
@@ -33,7 +34,19 @@ struct MeshDev {
   const double *hgeo;   // [6][nt]: h_i = 2|K| / l_i (i = 0..2), then 1 / h_i
   const int8_t *limv;
   const int32_t *conn;
+  // edges, each once, ordered by the owning cell (the lower cell id of an
+  // interior edge; the cell of a boundary edge)
+  int64_t ne;
+  const int32_t *e_cell;   // [ne] owning cell
+  const int8_t *e_loc;     // [ne] its local edge
+  const int32_t *etile;    // [ntiles + 1] first edge owned by each tile of TPB cells
+  const int32_t *cedge;    // [3][nt] edge index of (cell, local edge)
 };
+
+// rows of the per-edge OE record ej[EJ_ROWS][ne]: beta, then sqrt of the
+// trapezoidal jump sums for q = rho, (m_n|m_t max | m1), (m2), E and j = 0..k
+constexpr int EJ_ROWS = 13;
+__host__ __device__ constexpr int ej_row(int q, int j, int K) { return 1 + q * (K + 1) + j; }
 
 template <typename Real> struct StateDev {
   double *avg;   // [4][nt]

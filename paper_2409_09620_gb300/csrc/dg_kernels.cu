@@ -145,15 +145,17 @@ static void rk_impl(cudaStream_t s, const MeshDev &m, const Phys &ph, StateDev<R
                                               sc, a, b, c_in);
 }
 template <int K, typename Real>
-static void stats_impl(cudaStream_t s, const MeshDev &m, StateDev<Real> uh, double *part_dev, Scalars *sc) {
-  k_stats<K, Real><<<nblocks(m.nt), TPB, 0, s>>>(m, uh, part_dev, sc);
+static void stats_impl(cudaStream_t s, const MeshDev &m, const Phys &ph, StateDev<Real> uh, double *part_dev,
+                       const void *vd, const void *hs, void *ej, Scalars *sc, double c_out) {
+  k_stats<K, Real><<<nblocks(m.nt), TPB, 0, s>>>(m, ph, uh, part_dev, (const Real *)vd, (const Real *)hs, (Real *)ej,
+                                                 sc, c_out);
 }
 template <int K, typename Real>
 static void oebp_impl(cudaStream_t s, const MeshDev &m, const Phys &ph, StateDev<Real> uh, StateDev<Real> out,
-                      const void *vd, const void *hs, void *tr, double *pa, long long *pc, Scalars *sc, int do_oe,
-                      int do_bp, double c_out) {
-  k_oe_bp<K, Real><<<nblocks(m.nt), TPB, 0, s>>>(m, ph, uh, out, (const Real *)vd, (const Real *)hs, (Real *)tr, pa,
-                                                 pc, sc, do_oe, do_bp, c_out);
+                      const void *ej, void *tr, double *pa, long long *pc, Scalars *sc, int do_oe, int do_bp,
+                      double c_out) {
+  k_oe_bp<K, Real><<<nblocks(m.nt), TPB, 0, s>>>(m, ph, uh, out, (const Real *)ej, (Real *)tr, pa, pc, sc, do_oe, do_bp,
+                                                 c_out);
 }
 
 #define DG_DISPATCH(K_, PREC_, CALL)                        \
@@ -186,24 +188,26 @@ void launch_fin_mean(const StageCtx &c) {
   k_fin_mean<<<1, FIN_THREADS, 0, c.stream>>>(c.part_sum, (int)nblocks(c.mesh.nt), c.sc);
 }
 
-void launch_stats_only(const StageCtx &c, const StateBuf &uh) {
-  DG_DISPATCH(c.k, c.prec, (stats_impl<KK, Real>(c.stream, c.mesh, {uh.avg, (Real *)uh.hi}, c.part_dev, c.sc)));
+void launch_stats_only(const StageCtx &c, const StateBuf &uh, double c_out) {
+  DG_DISPATCH(c.k, c.prec,
+              (stats_impl<KK, Real>(c.stream, c.mesh, c.phys, {uh.avg, (Real *)uh.hi}, c.part_dev, c.vd, c.hs, c.ej,
+                                    c.sc, c_out)));
 }
 
 void launch_fin_dev(const StageCtx &c) {
   k_fin_dev<<<1, FIN_THREADS, 0, c.stream>>>(c.part_dev, (int)nblocks(c.mesh.nt), c.sc, c.phys.oe == 2);
 }
 
-void launch_stats(const StageCtx &c, const StateBuf &uh) {
-  launch_stats_only(c, uh);
+void launch_stats(const StageCtx &c, const StateBuf &uh, double c_out) {
+  launch_stats_only(c, uh, c_out);
   launch_fin_dev(c);
 }
 
 void launch_oe_bp_only(const StageCtx &c, const StateBuf &uh, const StateBuf &out, int do_oe, int do_bp,
                        double c_out) {
   DG_DISPATCH(c.k, c.prec,
-              (oebp_impl<KK, Real>(c.stream, c.mesh, c.phys, {uh.avg, (Real *)uh.hi}, {out.avg, (Real *)out.hi}, c.vd,
-                                   c.hs, c.tr, c.part_alpha, c.part_cnt, c.sc, do_oe, do_bp, c_out)));
+              (oebp_impl<KK, Real>(c.stream, c.mesh, c.phys, {uh.avg, (Real *)uh.hi}, {out.avg, (Real *)out.hi}, c.ej,
+                                   c.tr, c.part_alpha, c.part_cnt, c.sc, do_oe, do_bp, c_out)));
 }
 
 void launch_fin_alpha(const StageCtx &c, int stage) {

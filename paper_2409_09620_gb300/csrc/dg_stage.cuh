@@ -92,6 +92,7 @@ __device__ __forceinline__ void rk_tile(const MeshDev &m, const Phys &ph, StateD
 
     // ---- edge term: - sum_i l_i sum_nu w_nu Fhat Psi_l -------------------------
     double acc0[4] = {0.0, 0.0, 0.0, 0.0};
+    Real tv0[NQ][4];   // mixed form: per-point mode-0 contributions of one edge
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       const int32_t cn = m.conn[i * nt + Kc];
@@ -131,10 +132,24 @@ __device__ __forceinline__ void rk_tile(const MeshDev &m, const Phys &ph, StateD
         for (int c = 0; c < 4; ++c) {
           const Real fh = Real(0.5) * (fm[c] + fp[c] - alpha * (up[c] - um[c]));
           const Real tv = lw * fh;
-          acc0[c] -= double(tv);
+          if constexpr (sizeof(Real) == sizeof(double)) {
+            acc0[c] -= double(tv);
+          } else {
+            tv0[nu][c] = tv;
+          }
 #pragma unroll
           for (int l = 1; l < NB; ++l)
             acc[c][l] = cfma(-psi(l, edge_xi(i, gauss_s(NQ, nu)), edge_eta(i, gauss_s(NQ, nu))), tv, acc[c][l]);
+        }
+      }
+      if constexpr (sizeof(Real) != sizeof(double)) {
+        // FP32 edge contributions summed in an order that is symmetric under
+        // the neighbour's reversed point order, so the neighbour's sum is the
+        // exact negation; the FP64 average accumulates one term per edge
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const Real se = NQ == 3 ? (tv0[0][c] + tv0[2][c]) + tv0[1][c] : tv0[0][c] + tv0[NQ - 1][c];
+          acc0[c] -= double(se);
         }
       }
     }
@@ -239,28 +254,25 @@ __device__ __forceinline__ void stats_tile(const MeshDev &m, StateDev<Real> uh, 
     double off[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) off[c] = a0[c] - sc->mean[c];   // deviation of the cell mean
+    // deviations in the working precision; one conversion per cell
+    Real dr[5] = {Real(0), Real(0), Real(0), Real(0), Real(0)};
 #pragma unroll
     for (int mu = 0; mu < NV; ++mu) {
       Real u[4];
       eval_fixed<Real, NB>(off, hi, vol_xi(NV, mu), vol_eta(NV, mu), u);
-      const double r = fabs(double(u[0])), e = fabs(double(u[3]));
-      const double mm = sqrt(double(u[1]) * double(u[1]) + double(u[2]) * double(u[2]));
-      d[0] = fmax(d[0], r);
-      d[1] = fmax(d[1], mm);
-      d[2] = fmax(d[2], e);
-      d[3] = fmax(d[3], fabs(double(u[1])));
-      d[4] = fmax(d[4], fabs(double(u[2])));
+      dr[0] = fmax(dr[0], fabs(u[0]));
+      dr[1] = fmax(dr[1], sqrt(u[1] * u[1] + u[2] * u[2]));
+      dr[2] = fmax(dr[2], fabs(u[3]));
+      dr[3] = fmax(dr[3], fabs(u[1]));
+      dr[4] = fmax(dr[4], fabs(u[2]));
     }
+#pragma unroll
+    for (int q = 0; q < 5; ++q) d[q] = double(dr[q]);
   }
   block_reduce<5>(d, part_dev + 5 * tile, OpMax());
 }
 
-template <int K, typename Real>
-__global__ void __launch_bounds__(TPB) k_stats(MeshDev m, StateDev<Real> uh, double *__restrict__ part_dev,
-                                               const Scalars *__restrict__ sc) {
-  if (!sc->active) return;
-  stats_tile<K, Real>(m, uh, part_dev, sc, blockIdx.x);
-}
+
 
 // ==========================================================================
 // K3: RIOE + BP limiter + traces / alpha of the limited state
@@ -320,6 +332,120 @@ __device__ __forceinline__ void ghost_vertex(int tag, const Real val[4], const R
     for (int q = 0; q < 8; ++q) og[q] = grd[q];
 #pragma unroll
     for (int q = 0; q < 12; ++q) oh[q] = hes[q];
+  }
+}
+
+// --------------------------------------------------------------------------
+// OE jump data of one edge, computed once for both cells that share it: beta
+// (max spectral radius of both sides at both endpoints) and the square roots
+// of the trapezoidal sums 1/2 sum_{|alpha| = j} C_j^alpha1 [d^alpha q]^2 over
+// the two endpoints (eqs. OEScalar:Coef2 with the trapezoidal rule,
+// RIOESys:Coef1/Coef2), seen from the owning cell.  Jump sums are even in the
+// sign of the jump and of the normal, so both cells share them.
+// Edges [etile[tile], etile[tile + 1]) are processed in chunks of TPB.
+// --------------------------------------------------------------------------
+template <int K, typename Real>
+__device__ __forceinline__ void edge_tile(const MeshDev &m, const Phys &ph, const Real *__restrict__ vdi,
+                                          const Real *__restrict__ hsi, Real *__restrict__ ej,
+                                          const Scalars *__restrict__ sc, double c_out, int64_t tile) {
+  const int64_t nt = m.nt, ne = m.ne;
+  const int64_t e0 = m.etile[tile], e1 = m.etile[tile + 1];
+  const double t_out = sc->t + c_out * sc->dt;
+  const Real gamma = Real(ph.gamma);
+  const int cw = ph.oe == 2;
+  for (int64_t e = e0 + threadIdx.x; e < e1; e += TPB) {
+    const int64_t Kc = m.e_cell[e];
+    const int i = m.e_loc[e];
+    const int32_t cn = m.conn[i * nt + Kc];
+    const Real nx = Real(m.nrm[(2 * i) * nt + Kc]), ny = Real(m.nrm[(2 * i + 1) * nt + Kc]);
+    const Real *vme = vdi + Kc * 42;
+    Real hme[12], hot[12];
+#pragma unroll
+    for (int q = 0; q < 12; ++q) hme[q] = (K == 2) ? hsi[Kc * 12 + q] : Real(0);
+    const Real *vnb = nullptr;
+    int jn = 0;
+    if (cn >= 0) {
+      vnb = vdi + (int64_t)(cn >> 2) * 42;
+      jn = cn & 3;
+#pragma unroll
+      for (int q = 0; q < 12; ++q) hot[q] = (K == 2) ? hsi[(int64_t)(cn >> 2) * 12 + q] : Real(0);
+    }
+    Real Jq[4][K + 1];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int j = 0; j <= K; ++j) Jq[q][j] = Real(0);
+    Real beta = Real(0);
+#pragma unroll
+    for (int ev = 0; ev < 2; ++ev) {
+      const int ov = (i + 1 + ev) % 3;                 // v_c then v_d
+      Real val[4], grd[8], xv[4], xg[8], xh[12];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) val[c] = vme[ov * 14 + c];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) grd[q] = vme[ov * 14 + 4 + q];
+      const Real r_own = fabs(val[1] * nx + val[2] * ny) * vme[ov * 14 + 12] + vme[ov * 14 + 13];
+      Real r_oth;
+      if (cn >= 0) {
+        const int xvtx = (jn + 2 - ev) % 3;            // the neighbour's copy of this vertex
+#pragma unroll
+        for (int c = 0; c < 4; ++c) xv[c] = vnb[xvtx * 14 + c];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) xg[q] = vnb[xvtx * 14 + 4 + q];
+#pragma unroll
+        for (int q = 0; q < 12; ++q) xh[q] = hot[q];
+        r_oth = fabs(xv[1] * nx + xv[2] * ny) * vnb[xvtx * 14 + 12] + vnb[xvtx * 14 + 13];
+      } else {
+        double px = 0.0, py = 0.0;
+        if (cn == -7) { px = m.vxy[(2 * ov) * nt + Kc]; py = m.vxy[(2 * ov + 1) * nt + Kc]; }
+        ghost_vertex(-cn, val, grd, hme, nx, ny, px, py, t_out, ph, xv, xg, xh);
+        // a mirror or copied state has the same spectral radius
+        r_oth = cn >= -2 ? r_own : wave_speed(xv, nx, ny, gamma);
+      }
+      beta = fmax(beta, fmax(r_own, r_oth));
+      Real jv[4], jg[4][2], jh[4][3];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        jv[c] = val[c] - xv[c];
+        jg[c][0] = grd[2 * c] - xg[2 * c];
+        jg[c][1] = grd[2 * c + 1] - xg[2 * c + 1];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) jh[c][r] = hme[3 * c + r] - xh[3 * c + r];
+      }
+      if (!cw) {   // rotate the momentum jumps to (m_n, m_t) with the owner's normal
+        Real t0 = jv[1], t1 = jv[2];
+        jv[1] = t0 * nx + t1 * ny; jv[2] = -t0 * ny + t1 * nx;
+#pragma unroll
+        for (int d = 0; d < 2; ++d) {
+          t0 = jg[1][d]; t1 = jg[2][d];
+          jg[1][d] = t0 * nx + t1 * ny; jg[2][d] = -t0 * ny + t1 * nx;
+        }
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          t0 = jh[1][r]; t1 = jh[2][r];
+          jh[1][r] = t0 * nx + t1 * ny; jh[2][r] = -t0 * ny + t1 * nx;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        Jq[q][0] += Real(0.5) * jv[q] * jv[q];
+        Jq[q][1] += Real(0.5) * (jg[q][0] * jg[q][0] + jg[q][1] * jg[q][1]);
+        if (K == 2)
+          Jq[q][K] += Real(0.5) * (jh[q][0] * jh[q][0] + Real(2) * jh[q][1] * jh[q][1] + jh[q][2] * jh[q][2]);
+      }
+    }
+    ej[e] = beta;
+#pragma unroll
+    for (int j = 0; j <= K; ++j) {
+      ej[ej_row(0, j, K) * ne + e] = sqrt(Jq[0][j]);
+      ej[ej_row(3, j, K) * ne + e] = sqrt(Jq[3][j]);
+      if (cw) {
+        ej[ej_row(1, j, K) * ne + e] = sqrt(Jq[1][j]);
+        ej[ej_row(2, j, K) * ne + e] = sqrt(Jq[2][j]);
+      } else {   // RIOE: delta_m = max(delta_mn, delta_mt) -> sqrt(max(J_mn, J_mt))
+        ej[ej_row(1, j, K) * ne + e] = sqrt(fmax(Jq[1][j], Jq[2][j]));
+      }
+    }
   }
 }
 
@@ -550,7 +676,7 @@ __device__ __forceinline__ void limit_and_trace_mixed(const MeshDev &m, const Ph
 
 template <int K, typename Real>
 __device__ __forceinline__ void oe_bp_tile(const MeshDev &m, const Phys &ph, StateDev<Real> uh, StateDev<Real> out,
-                                           const Real *__restrict__ vdi, const Real *__restrict__ hsi,
+                                           const Real *__restrict__ ej,
                                            Real *__restrict__ tr, double *__restrict__ part_alpha,
                                            long long *__restrict__ part_cnt, const Scalars *__restrict__ sc,
                                            int do_oe, int do_bp, double c_out, int64_t tile) {
@@ -587,111 +713,22 @@ __device__ __forceinline__ void oe_bp_tile(const MeshDev &m, const Phys &ph, Sta
       for (int c = 0; c < 4; ++c)
 #pragma unroll
         for (int j = 0; j <= K; ++j) sig[c][j] = Real(0);
-      const Real *vme = vdi + Kc * 42;
-      Real hme[12];
-#pragma unroll
-      for (int q = 0; q < 12; ++q) hme[q] = (K == 2) ? hsi[Kc * 12 + q] : Real(0);
-
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        const Real nx = nxs[i], ny = nys[i];
-        const int32_t cn = cns[i];
+        // beta and sqrt of the jump sums of this edge (edge_tile, shared by both cells)
+        const int64_t eid = m.cedge[i * nt + Kc];
         const Real h = Real(m.hgeo[i * nt + Kc]), ih = Real(m.hgeo[(3 + i) * nt + Kc]);
-        Real Jq[4][K + 1];
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-#pragma unroll
-          for (int j = 0; j <= K; ++j) Jq[q][j] = Real(0);
-        Real beta = Real(0);
-        Real hot[12];
-        const Real *vnb = nullptr;
-        int jn = 0;
-        if (cn >= 0) {
-          vnb = vdi + (int64_t)(cn >> 2) * 42;
-          jn = cn & 3;
-          if (K == 2) {
-#pragma unroll
-            for (int q = 0; q < 12; ++q) hot[q] = hsi[(int64_t)(cn >> 2) * 12 + q];
-          }
-        }
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          const int ov = (i + 1 + e) % 3;                 // v_c then v_d
-          Real val[4], grd[8], xv[4], xg[8], xh[12];
-#pragma unroll
-          for (int c = 0; c < 4; ++c) val[c] = vme[ov * 14 + c];
-#pragma unroll
-          for (int q = 0; q < 8; ++q) grd[q] = vme[ov * 14 + 4 + q];
-          // beta_K^(i): spectral radius |v.n| + c of both sides at both endpoints
-          const Real r_own = fabs(val[1] * nx + val[2] * ny) * vme[ov * 14 + 12] + vme[ov * 14 + 13];
-          Real r_oth;
-          if (cn >= 0) {
-            const int xvtx = (jn + 2 - e) % 3;            // the neighbour's copy of this vertex
-#pragma unroll
-            for (int c = 0; c < 4; ++c) xv[c] = vnb[xvtx * 14 + c];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) xg[q] = vnb[xvtx * 14 + 4 + q];
-#pragma unroll
-            for (int q = 0; q < 12; ++q) xh[q] = K == 2 ? hot[q] : Real(0);
-            r_oth = fabs(xv[1] * nx + xv[2] * ny) * vnb[xvtx * 14 + 12] + vnb[xvtx * 14 + 13];
-          } else {
-            double px = 0.0, py = 0.0;
-            if (cn == -7) { px = m.vxy[(2 * ov) * nt + Kc]; py = m.vxy[(2 * ov + 1) * nt + Kc]; }
-            ghost_vertex(-cn, val, grd, hme, nx, ny, px, py, t_out, ph, xv, xg, xh);
-            // a mirror or copied state has the same spectral radius
-            r_oth = cn >= -2 ? r_own : wave_speed(xv, nx, ny, gamma);
-          }
-          beta = fmax(beta, fmax(r_own, r_oth));
-          // jumps of (rho, m1, m2, E): value, gradient, Hessian
-          Real jv[4], jg[4][2], jh[4][3];
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            jv[c] = val[c] - xv[c];
-            jg[c][0] = grd[2 * c] - xg[2 * c];
-            jg[c][1] = grd[2 * c + 1] - xg[2 * c + 1];
-#pragma unroll
-            for (int r = 0; r < 3; ++r) jh[c][r] = hme[3 * c + r] - xh[3 * c + r];
-          }
-          if (!cw) {   // rotate the momentum jumps to (m_n, m_t) with K's normal
-            Real t0 = jv[1], t1 = jv[2];
-            jv[1] = t0 * nx + t1 * ny; jv[2] = -t0 * ny + t1 * nx;
-#pragma unroll
-            for (int d = 0; d < 2; ++d) {
-              t0 = jg[1][d]; t1 = jg[2][d];
-              jg[1][d] = t0 * nx + t1 * ny; jg[2][d] = -t0 * ny + t1 * nx;
-            }
-#pragma unroll
-            for (int r = 0; r < 3; ++r) {
-              t0 = jh[1][r]; t1 = jh[2][r];
-              jh[1][r] = t0 * nx + t1 * ny; jh[2][r] = -t0 * ny + t1 * nx;
-            }
-          }
-          // trapezoidal rule: 1/2 sum_alpha C_j^alpha1 [d^alpha q]^2 at each endpoint
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            Jq[q][0] += Real(0.5) * jv[q] * jv[q];
-            Jq[q][1] += Real(0.5) * (jg[q][0] * jg[q][0] + jg[q][1] * jg[q][1]);
-            if (K == 2)
-              Jq[q][K] += Real(0.5) * (jh[q][0] * jh[q][0] + Real(2) * jh[q][1] * jh[q][1] + jh[q][2] * jh[q][2]);
-          }
-        }
-        // delta_q^j = A^{k,j} h^j sqrt(J) / D_q, A^{k,j} = (2j + 1) / ((2k - 1) j!);
-        // RIOE: delta_m = max(delta_mn, delta_mt) = A h^j sqrt(max(J_mn, J_mt)) / D_m
-        const Real bh = beta * ih;
+        const Real bh = ej[eid] * ih;
+        // delta_q^j = A^{k,j} h^j sqrt(J) / D_q, A^{k,j} = (2j + 1) / ((2k - 1) j!)
         Real hj = Real(1);
 #pragma unroll
         for (int j = 0; j <= K; ++j) {
           const Real Ah = Real((2.0 * j + 1.0) / ((2.0 * K - 1.0) * (j == 2 ? 2.0 : 1.0))) * hj;
           Real dl[4];
-          dl[0] = Ah * iD[0] * sqrt(Jq[0][j]);
-          dl[3] = Ah * iD[3] * sqrt(Jq[3][j]);
-          if (cw) {
-            dl[1] = Ah * iD[1] * sqrt(Jq[1][j]);
-            dl[2] = Ah * iD[2] * sqrt(Jq[2][j]);
-          } else {
-            dl[1] = Ah * iD[1] * sqrt(fmax(Jq[1][j], Jq[2][j]));
-            dl[2] = dl[1];
-          }
+          dl[0] = Ah * iD[0] * ej[ej_row(0, j, K) * m.ne + eid];
+          dl[1] = Ah * iD[1] * ej[ej_row(1, j, K) * m.ne + eid];
+          dl[2] = cw ? Ah * iD[2] * ej[ej_row(2, j, K) * m.ne + eid] : dl[1];
+          dl[3] = Ah * iD[3] * ej[ej_row(3, j, K) * m.ne + eid];
 #pragma unroll
           for (int c = 0; c < 4; ++c)
             if (dl[c] != Real(0)) sig[c][j] += bh * dl[c];
@@ -836,14 +873,23 @@ __device__ __forceinline__ void oe_bp_tile(const MeshDev &m, const Phys &ph, Sta
   __syncthreads();
 }
 
+// OE statistics of the tile's cells and the jump data of the edges it owns
+template <int K, typename Real>
+__global__ void __launch_bounds__(TPB) k_stats(MeshDev m, Phys ph, StateDev<Real> uh, double *__restrict__ part_dev,
+                                               const Real *__restrict__ vdi, const Real *__restrict__ hsi,
+                                               Real *__restrict__ ej, const Scalars *__restrict__ sc, double c_out) {
+  if (!sc->active) return;
+  stats_tile<K, Real>(m, uh, part_dev, sc, blockIdx.x);
+  edge_tile<K, Real>(m, ph, vdi, hsi, ej, sc, c_out, blockIdx.x);
+}
+
 template <int K, typename Real>
 __global__ void __launch_bounds__(TPB) k_oe_bp(MeshDev m, Phys ph, StateDev<Real> uh, StateDev<Real> out,
-                                               const Real *__restrict__ vdi, const Real *__restrict__ hsi,
-                                               Real *__restrict__ tr, double *__restrict__ part_alpha,
-                                               long long *__restrict__ part_cnt, const Scalars *__restrict__ sc,
-                                               int do_oe, int do_bp, double c_out) {
+                                               const Real *__restrict__ ej, Real *__restrict__ tr,
+                                               double *__restrict__ part_alpha, long long *__restrict__ part_cnt,
+                                               const Scalars *__restrict__ sc, int do_oe, int do_bp, double c_out) {
   if (!sc->active) return;
-  oe_bp_tile<K, Real>(m, ph, uh, out, vdi, hsi, tr, part_alpha, part_cnt, sc, do_oe, do_bp, c_out, blockIdx.x);
+  oe_bp_tile<K, Real>(m, ph, uh, out, ej, tr, part_alpha, part_cnt, sc, do_oe, do_bp, c_out, blockIdx.x);
 }
 
 }  // namespace dg
