@@ -227,6 +227,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=10)
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-cfl-gain", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-rate", type=float, default=30.0)
     args = ap.parse_args()
@@ -415,6 +416,31 @@ def main():
                    "steps_total": int(sum(f["steps"] for f in infos))}
         srv.close()
 
+    # the paper's headline: optimal vs classical decomposition, steps and time to
+    # the same end time (BP time step of Sec. 5 with either CFL number)
+    cfl_gain = None
+    if not args.no_cfl_gain:
+        from paper_2409_09620_gb300 import workloads as W
+        cfl_gain = {"workload": "dmr720x180 (259,200 cells), FP64, RIOE + BP, to t = T"}
+        for k, T in ((1, 1e-3), (2, 1e-3)):
+            wl_g = W.dmr_workload(nx=720, ny=180, k=k)
+            m_g = N.Mesh.from_mesh(wl_g.mesh)
+            u_g = N.initial_state(m_g, wl_g)
+            res = {}
+            for name, dc in (("optimal", 0), ("classical", 1)):
+                sv = N.Solver(m_g, N.config_for(wl_g, decomp=dc), u_g)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                st_g, _ = sv.advance(T)
+                el = time.perf_counter() - t0
+                res[name] = {"steps": st_g["steps"], "seconds": el, "mean_dt": T / st_g["steps"]}
+                del sv
+            cfl_gain[f"P{k}"] = {"T": T, **{n: v for n, v in res.items()},
+                                 "mean_dt_ratio": res["classical"]["steps"] / res["optimal"]["steps"],
+                                 "time_ratio": res["classical"]["seconds"] / res["optimal"]["seconds"],
+                                 "min_cfl_area_ratio": m_g.min_cfl_area(k, 0) / m_g.min_cfl_area(k, 1)}
+        cfl_gain["paper_dmr_mean_dt_ratio"] = {"P1": 2.869570, "P2": 4.486689}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         wl_full = make_workload(args.workload, args.nx, args.ny)
@@ -433,7 +459,7 @@ def main():
                            "l2": "working set ~1.7 GB > 129 MB L2, no flush"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": 19 * args.steps, "clocks": clocks, "fp32": mixed, "batch": batch,
-                "serving": serving,
+                "serving": serving, "bp_cfl_gain": cfl_gain,
                 "peaks": {"source": peak_src, "hbm_gbs": peaks.get("hbm_gbs")},
                 "stats": {"limited_cells": st["limited_cells"], "cfl_breaches": st["cfl_breaches"],
                           "t": st["t"], "dt_last": st["dt_last"]}}

@@ -512,6 +512,7 @@ extern "C" int32_t dg_init(const dg_mesh *mesh, const dg_config *cfg, const doub
   ph.oe = cfg->oe;
   ph.bp = cfg->bp;
   ph.k = cfg->k;
+  ph.decomp = cfg->decomp;
   c.tr = s->tr;
   c.vd = s->vd;
   c.hs = s->hs;

@@ -58,7 +58,7 @@ struct Phys {
   double bc[4][4];
   double shock_x0, shock_cot, shock_vx;   // x_s(y, t) = x0 + y cot(angle) + t speed / sin(angle)
   int shock_pre, shock_post;
-  int oe, bp, k, pad;
+  int oe, bp, k, decomp;   // decomp: 0 optimal convex decomposition, 1 classical (ZXS)
 };
 
 // Device-resident scalars of one solver.
@@ -361,6 +361,30 @@ __device__ __forceinline__ void step_begin_thread(Scalars *sc) {
   } else {
     sc->dt = 0.0;
     sc->active = 0;
+  }
+}
+
+// Deviation from the average of the extra limiter point(s) of the classical
+// decomposition, from the deviations at the edge Gauss points (the first 3Q
+// rows of d): P1 has no internal term (its edge weights sum to one), so the
+// edge point 0 is repeated; P2 takes the weighted internal state u_* of
+// Sec. 4.1 with edge weights 1/9: u_* - ubar = -(1/9) sum w_nu dev / (1 - 3/9).
+template <int K, typename T, int ROWS>
+__device__ __forceinline__ void zxs_extra_points(T d[ROWS][4]) {
+  constexpr int NQ = K + 1, NE = 3 * NQ;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    T v;
+    if (K == 1) {
+      v = d[0][c];
+    } else {
+      T acc = T(0);
+#pragma unroll
+      for (int p = 0; p < NE; ++p) acc += T(gauss_w(NQ, p % NQ)) * d[p][c];
+      v = T(-1.0 / 6.0) * acc;
+    }
+    d[NE][c] = v;
+    d[NE + 1][c] = v;
   }
 }
 

@@ -517,18 +517,26 @@ __device__ __forceinline__ void limit_and_trace_mixed(const MeshDev &m, const Ph
       bool ok = true;
 #pragma unroll
       for (int p = 0; p < NE; ++p) ok = passes(df[p]) && ok;
+      float dx[NE + 2][4];
+      if (ph.decomp) {
 #pragma unroll
-      for (int p = 0; p < 2; ++p) {
-        float d[4];
+        for (int p = 0; p < NE; ++p)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          float sacc = 0.0f;
+          for (int c = 0; c < 4; ++c) dx[p][c] = df[p][c];
+        zxs_extra_points<K, float, NE + 2>(dx);
+      } else {
 #pragma unroll
-          for (int l = 1; l < NB; ++l) sacc = fmaf(float(psi(l, px[p], py[p])), hi[c][l], sacc);
-          d[c] = sacc;
-        }
-        ok = passes(d) && ok;
+        for (int p = 0; p < 2; ++p)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            float sacc = 0.0f;
+#pragma unroll
+            for (int l = 1; l < NB; ++l) sacc = fmaf(float(psi(l, px[p], py[p])), hi[c][l], sacc);
+            dx[NE + p][c] = sacc;
+          }
       }
+#pragma unroll
+      for (int p = 0; p < 2; ++p) ok = passes(dx[NE + p]) && ok;
       lim64 = !ok;
     }
   }
@@ -566,15 +574,19 @@ __device__ __forceinline__ void limit_and_trace_mixed(const MeshDev &m, const Ph
           d[i * NQ + nu][c] = sacc;
         }
       }
+    if (ph.decomp) {
+      zxs_extra_points<K, double, NE + 2>(d);
+    } else {
 #pragma unroll
-    for (int p = 0; p < 2; ++p)
+      for (int p = 0; p < 2; ++p)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        double sacc = 0.0;
+        for (int c = 0; c < 4; ++c) {
+          double sacc = 0.0;
 #pragma unroll
-        for (int l = 1; l < NB; ++l) sacc = fma(psi(l, px[p], py[p]), double(hi[c][l]), sacc);
-        d[NE + p][c] = sacc;
-      }
+          for (int l = 1; l < NB; ++l) sacc = fma(psi(l, px[p], py[p]), double(hi[c][l]), sacc);
+          d[NE + p][c] = sacc;
+        }
+    }
     const double r22 = 2.384185791015625e-07;   // 2^-22: |Psi| <= 4 times the FP32 half-ulp 2^-24
     const double Ebar = int_energy(a0);
     double rmin = INFINITY;
@@ -604,25 +616,38 @@ __device__ __forceinline__ void limit_and_trace_mixed(const MeshDev &m, const Ph
     }
     // verify the stored FP32 modes in FP64 at every point of the set
     bool bad = false;
-    double ud[NE][4];
+    double ud[NE][4], vd2[NE + 2][4];
+#pragma unroll
+    for (int p = 0; p < NE; ++p) {
+      const int i = p / NQ, nu = p % NQ;
+      const double xi = edge_xi(i, gauss_s(NQ, nu)), eta = edge_eta(i, gauss_s(NQ, nu));
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        double sacc = 0.0;
+#pragma unroll
+        for (int l = 1; l < NB; ++l) sacc = cfma(psi(l, xi, eta), double(hs[c][l]), sacc);
+        vd2[p][c] = sacc;
+        ud[p][c] = a0[c] + sacc;
+      }
+    }
+    if (ph.decomp) {
+      zxs_extra_points<K, double, NE + 2>(vd2);
+    } else {
+#pragma unroll
+      for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          double sacc = 0.0;
+#pragma unroll
+          for (int l = 1; l < NB; ++l) sacc = fma(psi(l, px[p], py[p]), double(hs[c][l]), sacc);
+          vd2[NE + p][c] = sacc;
+        }
+    }
 #pragma unroll
     for (int p = 0; p < NE + 2; ++p) {
       double w[4];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        double sacc = a0[c];
-        if (p < NE) {
-          const int i = p / NQ, nu = p % NQ;
-          const double xi = edge_xi(i, gauss_s(NQ, nu)), eta = edge_eta(i, gauss_s(NQ, nu));
-#pragma unroll
-          for (int l = 1; l < NB; ++l) sacc = cfma(psi(l, xi, eta), double(hs[c][l]), sacc);
-          ud[p][c] = sacc;
-        } else {
-#pragma unroll
-          for (int l = 1; l < NB; ++l) sacc = fma(psi(l, px[p - NE], py[p - NE]), double(hs[c][l]), sacc);
-        }
-        w[c] = sacc;
-      }
+      for (int c = 0; c < 4; ++c) w[c] = a0[c] + vd2[p][c];
       if (!(w[0] > 0.0) || !(int_energy(w) > 0.0)) bad = true;
     }
     if (bad) {
@@ -783,15 +808,19 @@ __device__ __forceinline__ void oe_bp_tile(const MeshDev &m, const Phys &ph, Sta
         } else {
           px[0] = m.node[Kc]; py[0] = m.node[nt + Kc]; px[1] = m.node[2 * nt + Kc]; py[1] = m.node[3 * nt + Kc];
         }
+        if (ph.decomp) {
+          zxs_extra_points<K, double, NE + 2>(dev);
+        } else {
   #pragma unroll
-        for (int p = 0; p < 2; ++p)
+          for (int p = 0; p < 2; ++p)
   #pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            double s = 0.0;
+            for (int c = 0; c < 4; ++c) {
+              double s = 0.0;
   #pragma unroll
-            for (int l = 1; l < NB; ++l) s = fma(psi(l, px[p], py[p]), double(hi[c][l]), s);
-            dev[NE + p][c] = s;
-          }
+              for (int l = 1; l < NB; ++l) s = fma(psi(l, px[p], py[p]), double(hi[c][l]), s);
+              dev[NE + p][c] = s;
+            }
+        }
         const double Ebar = int_energy(a0);
         if (!(a0[0] > 0.0) || !(Ebar > 0.0)) {
           cnt[1] = 1;

@@ -63,7 +63,7 @@ def test_mixed_conserves_averages(oracle_mod, N, k):
 
 
 @pytest.mark.parametrize("k", [1, 2])
-@pytest.mark.parametrize("case", ["sedov", "dmr", "riemann"])
+@pytest.mark.parametrize("case", ["sedov", "dmr", "riemann", "sedov-zxs"])
 def test_mixed_bounds_hold_exactly(oracle_mod, N, k, case):
     """After every step the stored FP32 modes (with FP64 averages), evaluated in
     FP64 by the oracle at every point of the optimal-decomposition set, have
@@ -71,9 +71,15 @@ def test_mixed_bounds_hold_exactly(oracle_mod, N, k, case):
     O = oracle_mod
     wl = {"sedov": lambda: W.sedov_workload(n=16, k=k),
           "dmr": lambda: W.dmr_workload(nx=30, ny=10, k=k),
-          "riemann": lambda: W.riemann4_workload(n=14, k=k)}[case]()
-    om, u0, mesh, s32 = _solvers(O, N, wl)
-    cf = O.config_for(wl)
+          "riemann": lambda: W.riemann4_workload(n=14, k=k),
+          "sedov-zxs": lambda: W.sedov_workload(n=16, k=k)}[case]()
+    decomp = 1 if case.endswith("zxs") else 0
+    O_ = O
+    om = O_.OracleMesh.from_mesh(wl.mesh)
+    u0 = O_.project_workload(om, wl)
+    mesh = N.Mesh.from_mesh(wl.mesh)
+    s32 = N.Solver(mesh, N.config_for(wl, precision=N.PREC_MIXED, decomp=decomp), u0)
+    cf = O.config_for(wl, decomp=decomp)
     limited = 0
     for _ in range(15):
         st, _ = s32.advance(10.0, max_steps=1)

@@ -260,3 +260,40 @@ def test_errors(N):
     with pytest.raises(N.DGError) as e:
         N.Solver(mesh, N.make_config(3), np.zeros((4, 6, 1)))
     assert e.value.code == N.DG_EINVAL
+
+
+@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("case", ["vortex", "sedov", "dmr"])
+def test_classical_decomposition_step(oracle_mod, N, k, case):
+    """Classical (Zhang-Xia-Shu) decomposition: its CFL number (Sec. 4.3
+    remarks) and limiter point set (Sec. 4.4: edge Gauss points, plus the
+    weighted internal state for P2), one step vs the oracle."""
+    O = oracle_mod
+    wl = _cases()[case](k)
+    om, u0, mesh, solver = _setup(O, N, wl, decomp=1)
+    cf = O.config_for(wl, decomp=1)
+    st, _ = solver.advance(10.0, max_steps=1)
+    ug, tg = solver.get_state()
+    uo, to, dto, cnt, rc = om.step(cf, u0, 0.0, 10.0)
+    assert rc == 0
+    np.testing.assert_allclose(tg, to, rtol=1e-13)
+    assert rel_err(ug, uo) < TOL1
+    u = _perturbed(u0, 8, amp=0.8 if k == 1 else 0.4)
+    got, cg = solver.op_limit(u)
+    exp, co = om.limit(cf, u)
+    assert np.array_equal(cg, co) and co[0] > 0
+    assert rel_err(got, exp) < TOL1
+
+
+@pytest.mark.parametrize("k,lo,hi", [(1, 2.0, 3.0), (2, 3.8038, 4.5)])
+def test_bp_time_step_ratio(oracle_mod, N, k, lo, hi):
+    """The optimal decomposition's BP time step over the classical one, for
+    the same state (the paper's headline gain, Fig. 1744 ranges)."""
+    wl = W.dmr_workload(nx=48, ny=12, k=k)
+    om, u0, mesh, s_opt = _setup(oracle_mod, N, wl)
+    s_zxs = N.Solver(mesh, N.config_for(wl, decomp=1), u0)
+    a, _ = s_opt.advance(10.0, max_steps=1)
+    b, _ = s_zxs.advance(10.0, max_steps=1)
+    r = a["dt_last"] / b["dt_last"]
+    assert lo - 1e-9 <= r <= hi + 1e-9
+    np.testing.assert_allclose(r, mesh.min_cfl_area(k, 0) / mesh.min_cfl_area(k, 1), rtol=1e-12)
