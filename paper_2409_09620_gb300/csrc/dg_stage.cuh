@@ -912,8 +912,10 @@ __global__ void __launch_bounds__(TPB) k_stats(MeshDev m, Phys ph, StateDev<Real
   edge_tile<K, Real>(m, ph, vdi, hsi, ej, sc, c_out, blockIdx.x);
 }
 
+// the FP32 form is latency-bound: ask for three resident blocks per SM
 template <int K, typename Real>
-__global__ void __launch_bounds__(TPB) k_oe_bp(MeshDev m, Phys ph, StateDev<Real> uh, StateDev<Real> out,
+__global__ void __launch_bounds__(TPB, sizeof(Real) == 4 ? 3 : 1) k_oe_bp(MeshDev m, Phys ph, StateDev<Real> uh,
+                                                                        StateDev<Real> out,
                                                const Real *__restrict__ ej, Real *__restrict__ tr,
                                                double *__restrict__ part_alpha, long long *__restrict__ part_cnt,
                                                const Scalars *__restrict__ sc, int do_oe, int do_bp, double c_out) {

@@ -250,8 +250,11 @@ class Solver:
         _check(lib().dg_sync(self.h, C.byref(st)))
         return st.as_dict()
 
-    def get_state(self):
-        u = np.empty((4, self.nb, self.mesh.nt))
+    def get_state(self, out=None):
+        """Host copy of the state; `out` (C-contiguous float64, e.g. pinned memory) is written in place."""
+        u = np.empty((4, self.nb, self.mesh.nt)) if out is None else out
+        if u.dtype != np.float64 or not u.flags["C_CONTIGUOUS"] or u.size != 4 * self.nb * self.mesh.nt:
+            raise ValueError("out must be a C-contiguous float64 array of the state's size")
         t = dbl()
         _check(lib().dg_get_state(self.h, _p(u), u.size, C.byref(t)))
         return u, t.value
