@@ -58,12 +58,15 @@ struct dg_mesh {
   int64_t ne = 0;
   int32_t *e_cell = nullptr, *etile = nullptr, *cedge = nullptr;
   int8_t *e_loc = nullptr;
+  float *jinv_f = nullptr, *nrm_f = nullptr, *len_f = nullptr, *hgeo_f = nullptr;
+  double *iarea = nullptr;
   double min_ca[4] = {0, 0, 0, 0};   // (P1 optimal, P1 ZXS, P2 optimal, P2 ZXS)
   double area_total = 0.0;
   ~dg_mesh() {
     cudaFree(area); cudaFree(jinv); cudaFree(nrm); cudaFree(len); cudaFree(vxy); cudaFree(node);
     cudaFree(c_area); cudaFree(limv); cudaFree(conn); cudaFree(hgeo);
     cudaFree(e_cell); cudaFree(e_loc); cudaFree(etile); cudaFree(cedge);
+    cudaFree(jinv_f); cudaFree(nrm_f); cudaFree(len_f); cudaFree(hgeo_f); cudaFree(iarea);
   }
 };
 
@@ -226,6 +229,11 @@ extern "C" int32_t dg_mesh_create(int64_t nv, const double *xy, int64_t nt, cons
   MTRY(dalloc(&m->c_area, 4 * nt));
   MTRY(dalloc(&m->limv, 2 * nt));
   MTRY(dalloc(&m->conn, 3 * nt));
+  MTRY(dalloc(&m->jinv_f, 4 * nt));
+  MTRY(dalloc(&m->nrm_f, 6 * nt));
+  MTRY(dalloc(&m->len_f, 3 * nt));
+  MTRY(dalloc(&m->hgeo_f, 6 * nt));
+  MTRY(dalloc(&m->iarea, nt));
   MTRY(dalloc(&m->e_cell, m->ne));
   MTRY(dalloc(&m->e_loc, m->ne));
   MTRY(dalloc(&m->etile, ntiles + 1));
@@ -238,7 +246,8 @@ extern "C" int32_t dg_mesh_create(int64_t nv, const double *xy, int64_t nt, cons
   MTRY(dalloc(&mins, 4));
   MTRY(cudaMemcpy(m->vxy, m->vxy_host.data(), sizeof(double) * 6 * nt, cudaMemcpyHostToDevice));
   MTRY(cudaMemcpy(m->conn, conn.data(), sizeof(int32_t) * 3 * nt, cudaMemcpyHostToDevice));
-  GeomPtrs g{m->area, m->jinv, m->nrm, m->len, m->hgeo, m->node, m->c_area, m->limv};
+  GeomPtrs g{m->area,   m->jinv,  m->nrm,   m->len,    m->hgeo, m->node, m->c_area,
+             m->limv,   m->jinv_f, m->nrm_f, m->len_f, m->hgeo_f, m->iarea};
   launch_geometry(nullptr, nt, m->vxy, g, part, mins);
   MTRY(cudaGetLastError());
   MTRY(cudaMemcpy(m->min_ca, mins, sizeof(double) * 4, cudaMemcpyDeviceToHost));
@@ -481,9 +490,9 @@ extern "C" int32_t dg_init(const dg_mesh *mesh, const dg_config *cfg, const doub
   STRY(alloc_state(s, &s->uh));
   STRY(alloc_state(s, &s->us));
   STRY(cudaMalloc(&s->tr, rs * nt * 3 * nq * 8));
-  STRY(cudaMalloc(&s->vd, rs * nt * 42));
+  STRY(cudaMalloc(&s->vd, rs * nt * VD_CELL));
   STRY(cudaMalloc(&s->hs, rs * nt * 12));
-  STRY(cudaMalloc(&s->ej, rs * std::max<int64_t>(mesh->ne, 1) * EJ_ROWS));
+  STRY(cudaMalloc(&s->ej, rs * std::max<int64_t>(mesh->ne, 1) * EJ_STRIDE));
   STRY(dalloc(&s->part_sum, 4 * nblk));
   STRY(dalloc(&s->part_dev, 5 * nblk));
   STRY(dalloc(&s->part_alpha, nblk));
@@ -496,7 +505,7 @@ extern "C" int32_t dg_init(const dg_mesh *mesh, const dg_config *cfg, const doub
   c.prec = cfg->precision;
   c.mesh = MeshDev{nt,         mesh->area, mesh->jinv,   mesh->nrm,   mesh->len,   mesh->vxy,  mesh->node,
                    mesh->hgeo, mesh->limv, mesh->conn,   mesh->ne,    mesh->e_cell, mesh->e_loc, mesh->etile,
-                   mesh->cedge};
+                   mesh->cedge, mesh->jinv_f, mesh->nrm_f, mesh->len_f, mesh->hgeo_f, mesh->iarea};
   Phys &ph = c.phys;
   std::memset(&ph, 0, sizeof(ph));
   ph.gamma = cfg->gamma;

@@ -9,10 +9,10 @@
 //             limv[2][nt] (P1 limiter vertices), conn[3][nt] (neighbour << 2 | its edge, or -tag)
 //   exchange  tr[nt][3][Q][8]  traces of the stage input at edge Gauss points:
 //                              u (4) and F(u).n_i (4), written by the cell that owns them
-//             vd[nt][3][14]    value (4), physical gradient (8), 1/rho and sound speed
-//                              of u_h at each vertex
+//             vd[nt][3][16]    value (4), physical gradient (8), 1/rho and sound speed
+//                              of u_h at each vertex (2 padding values)
 //             hs[nt][12]       physical Hessian (xx, xy, yy) of u_h per component (P2)
-//             ej[13][ne]       per edge: beta and the square roots of the OE jump sums
+//             ej[ne][16]       per edge: beta and the square roots of the OE jump sums
 // Every kernel is one thread per cell; reductions are per-block partials
 // reduced in a fixed order, so results are bitwise reproducible.
 #pragma once
@@ -41,12 +41,63 @@ struct MeshDev {
   const int8_t *e_loc;     // [ne] its local edge
   const int32_t *etile;    // [ntiles + 1] first edge owned by each tile of TPB cells
   const int32_t *cedge;    // [3][nt] edge index of (cell, local edge)
+  // FP32 copies of the geometry the mixed-precision kernels read (the same
+  // rounded values, without a conversion per read), and 1/|K| in FP64
+  const float *jinv_f, *nrm_f, *len_f, *hgeo_f;
+  const double *iarea;
 };
 
-// rows of the per-edge OE record ej[EJ_ROWS][ne]: beta, then sqrt of the
-// trapezoidal jump sums for q = rho, (m_n|m_t max | m1), (m2), E and j = 0..k
-constexpr int EJ_ROWS = 13;
+// geometry in the working precision of a kernel
+template <typename Real> struct Geo;
+template <> struct Geo<double> {
+  static __device__ __forceinline__ const double *jinv(const MeshDev &m) { return m.jinv; }
+  static __device__ __forceinline__ const double *nrm(const MeshDev &m) { return m.nrm; }
+  static __device__ __forceinline__ const double *len(const MeshDev &m) { return m.len; }
+  static __device__ __forceinline__ const double *hgeo(const MeshDev &m) { return m.hgeo; }
+};
+template <> struct Geo<float> {
+  static __device__ __forceinline__ const float *jinv(const MeshDev &m) { return m.jinv_f; }
+  static __device__ __forceinline__ const float *nrm(const MeshDev &m) { return m.nrm_f; }
+  static __device__ __forceinline__ const float *len(const MeshDev &m) { return m.len_f; }
+  static __device__ __forceinline__ const float *hgeo(const MeshDev &m) { return m.hgeo_f; }
+};
+
+// per-edge OE record ej[ne][EJ_STRIDE]: beta, then sqrt of the trapezoidal
+// jump sums for q = rho, (m_n|m_t max | m1), (m2), E and j = 0..k (13 used)
+constexpr int EJ_STRIDE = 16;
 __host__ __device__ constexpr int ej_row(int q, int j, int K) { return 1 + q * (K + 1) + j; }
+// per-cell vertex record vd[nt][3][VD_STRIDE]: value (4), gradient (8), 1/rho, sound speed
+constexpr int VD_STRIDE = 16;
+constexpr int VD_CELL = 3 * VD_STRIDE;
+
+// 16-byte vector loads and stores of N consecutive values (N a multiple of 16/sizeof(T))
+template <typename T> struct Vec16;
+template <> struct Vec16<float> {
+  using type = float4;
+  static constexpr int n = 4;
+  static __device__ __forceinline__ void get(const float4 &v, float *o) { o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w; }
+  static __device__ __forceinline__ float4 make(const float *i) { return make_float4(i[0], i[1], i[2], i[3]); }
+};
+template <> struct Vec16<double> {
+  using type = double2;
+  static constexpr int n = 2;
+  static __device__ __forceinline__ void get(const double2 &v, double *o) { o[0] = v.x; o[1] = v.y; }
+  static __device__ __forceinline__ double2 make(const double *i) { return make_double2(i[0], i[1]); }
+};
+template <int N, typename T>
+__device__ __forceinline__ void vload(const T *__restrict__ p, T out[N]) {
+  constexpr int L = Vec16<T>::n;
+  const typename Vec16<T>::type *q = reinterpret_cast<const typename Vec16<T>::type *>(p);
+#pragma unroll
+  for (int k = 0; k < N / L; ++k) Vec16<T>::get(q[k], out + k * L);
+}
+template <int N, typename T>
+__device__ __forceinline__ void vstore(T *__restrict__ p, const T in[N]) {
+  constexpr int L = Vec16<T>::n;
+  typename Vec16<T>::type *q = reinterpret_cast<typename Vec16<T>::type *>(p);
+#pragma unroll
+  for (int k = 0; k < N / L; ++k) q[k] = Vec16<T>::make(in + k * L);
+}
 
 template <typename Real> struct StateDev {
   double *avg;   // [4][nt]

@@ -12,6 +12,8 @@ namespace dg {
 struct GeomPtrs {
   double *area, *jinv, *nrm, *len, *hgeo, *node, *c_area;
   int8_t *limv;
+  float *jinv_f, *nrm_f, *len_f, *hgeo_f;
+  double *iarea;
 };
 
 // a modal state: FP64 averages [4][nt] + higher modes [4][nb-1][nt] (double or float)

@@ -14,7 +14,9 @@ struct OpMinD { __device__ double operator()(double a, double b) const { return 
 // ==========================================================================
 __global__ void __launch_bounds__(TPB) k_geometry(int64_t nt, const double *__restrict__ vxy, double *area,
                                                   double *jinv, double *nrm, double *len, double *hgeo,
-                                                  double *node, int8_t *limv, double *c_area, double *part_min) {
+                                                  double *node, int8_t *limv, double *c_area, double *part_min,
+                                                  float *jinv_f, float *nrm_f, float *len_f, float *hgeo_f,
+                                                  double *iarea) {
   const int64_t K = (int64_t)blockIdx.x * TPB + threadIdx.x;
   double mins[4] = {INFINITY, INFINITY, INFINITY, INFINITY};
   if (K < nt) {
@@ -76,6 +78,16 @@ __global__ void __launch_bounds__(TPB) k_geometry(int64_t nt, const double *__re
       node[(2 * s) * nt + K] = bary[1];
       node[(2 * s + 1) * nt + K] = bary[2];
     }
+    iarea[K] = 1.0 / ar;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) jinv_f[q * nt + K] = float(jinv[q * nt + K]);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      nrm_f[q * nt + K] = float(nrm[q * nt + K]);
+      hgeo_f[q * nt + K] = float(hgeo[q * nt + K]);
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) len_f[q * nt + K] = float(len[q * nt + K]);
     const double cs[4] = {2.0 / (3.0 * (l1 + l2)), 1.0 / (9.0 * lb), 2.0 / (9.0 * lb + 3.0 * lh), 1.0 / (27.0 * lb)};
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -133,7 +145,8 @@ static inline unsigned nblocks(int64_t nt) { return (unsigned)((nt + TPB - 1) / 
 void launch_geometry(cudaStream_t s, int64_t nt, const double *vxy, const GeomPtrs &g, double *part_min,
                      double *out_min4) {
   const unsigned nb = nblocks(nt);
-  k_geometry<<<nb, TPB, 0, s>>>(nt, vxy, g.area, g.jinv, g.nrm, g.len, g.hgeo, g.node, g.limv, g.c_area, part_min);
+  k_geometry<<<nb, TPB, 0, s>>>(nt, vxy, g.area, g.jinv, g.nrm, g.len, g.hgeo, g.node, g.limv, g.c_area, part_min,
+                                g.jinv_f, g.nrm_f, g.len_f, g.hgeo_f, g.iarea);
   k_fin_min4<<<1, FIN_THREADS, 0, s>>>(part_min, (int)nb, out_min4);
 }
 

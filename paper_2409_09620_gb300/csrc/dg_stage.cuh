@@ -58,8 +58,8 @@ __device__ __forceinline__ void rk_tile(const MeshDev &m, const Phys &ph, StateD
     const double dt = sc->dt, alpha_d = sc->alpha, t_in = sc->t + c_in * sc->dt;
     const Real alpha = Real(alpha_d), gm1 = Real(ph.gamma - 1.0);
     const double area = m.area[Kc];
-    const Real jx = Real(m.jinv[Kc]), jy = Real(m.jinv[nt + Kc]);
-    const Real ex = Real(m.jinv[2 * nt + Kc]), ey = Real(m.jinv[3 * nt + Kc]);
+    const Real *gj = Geo<Real>::jinv(m);
+    const Real jx = gj[Kc], jy = gj[nt + Kc], ex = gj[2 * nt + Kc], ey = gj[3 * nt + Kc];
     double v0[4];
     Real cv[4][NB];
     load_state<Real, NB>(v, nt, Kc, v0, cv);
@@ -96,20 +96,21 @@ __device__ __forceinline__ void rk_tile(const MeshDev &m, const Phys &ph, StateD
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       const int32_t cn = m.conn[i * nt + Kc];
-      const Real nx = Real(m.nrm[(2 * i) * nt + Kc]), ny = Real(m.nrm[(2 * i + 1) * nt + Kc]);
-      const Real li = Real(m.len[i * nt + Kc]);
+      const Real nx = Geo<Real>::nrm(m)[(2 * i) * nt + Kc], ny = Geo<Real>::nrm(m)[(2 * i + 1) * nt + Kc];
+      const Real li = Geo<Real>::len(m)[i * nt + Kc];
 #pragma unroll
       for (int nu = 0; nu < NQ; ++nu) {
-        const Real *own = tr + ((Kc * 3 + i) * NQ + nu) * 8;
-        Real um[4], fm[4], up[4], fp[4];
+        Real ow[8], um[4], fm[4], up[4], fp[4];
+        vload<8>(tr + ((Kc * 3 + i) * NQ + nu) * 8, ow);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) { um[q] = own[q]; fm[q] = own[4 + q]; }
+        for (int q = 0; q < 4; ++q) { um[q] = ow[q]; fm[q] = ow[4 + q]; }
         if (cn >= 0) {
           const int64_t nb = cn >> 2;
           const int j = cn & 3;
-          const Real *oth = tr + ((nb * 3 + j) * NQ + (NQ - 1 - nu)) * 8;
+          Real ot[8];
+          vload<8>(tr + ((nb * 3 + j) * NQ + (NQ - 1 - nu)) * 8, ot);
 #pragma unroll
-          for (int q = 0; q < 4; ++q) { up[q] = oth[q]; fp[q] = -oth[4 + q]; }
+          for (int q = 0; q < 4; ++q) { up[q] = ot[q]; fp[q] = -ot[4 + q]; }
         } else {
           double px = 0.0, py = 0.0;
           if (cn == -7) {
@@ -158,7 +159,7 @@ __device__ __forceinline__ void rk_tile(const MeshDev &m, const Phys &ph, StateD
     double un0[4];
     Real cu[4][NB];
     load_state<Real, NB>(un, nt, Kc, un0, cu);
-    const double dta = dt / area;
+    const double dta = dt * m.iarea[Kc];
     double h0[4];
     Real hh[4][NB];
 #pragma unroll
@@ -169,18 +170,19 @@ __device__ __forceinline__ void rk_tile(const MeshDev &m, const Phys &ph, StateD
       hh[c][0] = Real(0);
 #pragma unroll
       for (int l = 1; l < NB; ++l) {
-        const Real s = Real(dta * inv_mass_c(l));
+        const Real s = sizeof(Real) == sizeof(double) ? Real(dta * inv_mass_c(l)) : Real(dta) * Real(inv_mass_c(l));
         hh[c][l] = Real(a) * cu[c][l] + Real(b) * (cv[c][l] + s * acc[c][l]);
         uh.hi[(c * (NB - 1) + (l - 1)) * nt + Kc] = hh[c][l];
       }
     }
 
     // ---- vertex derivatives of u_h for the OE jumps ------------------------------
-    Real *vo = vdo + Kc * 42;
+    Real *vo = vdo + Kc * VD_CELL;
     const Real gamma = Real(ph.gamma);
 #pragma unroll
     for (int vv = 0; vv < 3; ++vv) {
       const double xi = vert_xi(vv), eta = vert_eta(vv);
+      Real rec[VD_STRIDE];
       Real val4[4];
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
@@ -192,9 +194,9 @@ __device__ __forceinline__ void rk_tile(const MeshDev &m, const Phys &ph, StateD
           ge = cfma(psi_y(l, xi, eta), hh[c][l], ge);
         }
         val4[c] = val;
-        vo[vv * 14 + c] = val;
-        vo[vv * 14 + 4 + 2 * c] = gx * jx + ge * ex;
-        vo[vv * 14 + 5 + 2 * c] = gx * jy + ge * ey;
+        rec[c] = val;
+        rec[4 + 2 * c] = gx * jx + ge * ex;
+        rec[5 + 2 * c] = gx * jy + ge * ey;
       }
       // 1/rho and sound speed at the vertex, for the wave speeds beta of the OE (+inf for rho <= 0)
       Real ri = Real(0), cs = Real(INFINITY);
@@ -204,8 +206,11 @@ __device__ __forceinline__ void rk_tile(const MeshDev &m, const Phys &ph, StateD
         p = p > Real(0) ? p : Real(0);
         cs = sqrt(gamma * p * ri);
       }
-      vo[vv * 14 + 12] = ri;
-      vo[vv * 14 + 13] = cs;
+      rec[12] = ri;
+      rec[13] = cs;
+      rec[14] = Real(0);
+      rec[15] = Real(0);
+      vstore<VD_STRIDE>(vo + vv * VD_STRIDE, rec);
     }
     if (K == 2) {
       Real *ho = hso + Kc * 12;
@@ -348,7 +353,7 @@ template <int K, typename Real>
 __device__ __forceinline__ void edge_tile(const MeshDev &m, const Phys &ph, const Real *__restrict__ vdi,
                                           const Real *__restrict__ hsi, Real *__restrict__ ej,
                                           const Scalars *__restrict__ sc, double c_out, int64_t tile) {
-  const int64_t nt = m.nt, ne = m.ne;
+  const int64_t nt = m.nt;
   const int64_t e0 = m.etile[tile], e1 = m.etile[tile + 1];
   const double t_out = sc->t + c_out * sc->dt;
   const Real gamma = Real(ph.gamma);
@@ -357,15 +362,15 @@ __device__ __forceinline__ void edge_tile(const MeshDev &m, const Phys &ph, cons
     const int64_t Kc = m.e_cell[e];
     const int i = m.e_loc[e];
     const int32_t cn = m.conn[i * nt + Kc];
-    const Real nx = Real(m.nrm[(2 * i) * nt + Kc]), ny = Real(m.nrm[(2 * i + 1) * nt + Kc]);
-    const Real *vme = vdi + Kc * 42;
+    const Real nx = Geo<Real>::nrm(m)[(2 * i) * nt + Kc], ny = Geo<Real>::nrm(m)[(2 * i + 1) * nt + Kc];
+    const Real *vme = vdi + Kc * VD_CELL;
     Real hme[12], hot[12];
 #pragma unroll
     for (int q = 0; q < 12; ++q) hme[q] = (K == 2) ? hsi[Kc * 12 + q] : Real(0);
     const Real *vnb = nullptr;
     int jn = 0;
     if (cn >= 0) {
-      vnb = vdi + (int64_t)(cn >> 2) * 42;
+      vnb = vdi + (int64_t)(cn >> 2) * VD_CELL;
       jn = cn & 3;
 #pragma unroll
       for (int q = 0; q < 12; ++q) hot[q] = (K == 2) ? hsi[(int64_t)(cn >> 2) * 12 + q] : Real(0);
@@ -379,22 +384,25 @@ __device__ __forceinline__ void edge_tile(const MeshDev &m, const Phys &ph, cons
 #pragma unroll
     for (int ev = 0; ev < 2; ++ev) {
       const int ov = (i + 1 + ev) % 3;                 // v_c then v_d
-      Real val[4], grd[8], xv[4], xg[8], xh[12];
+      Real rec[VD_STRIDE], val[4], grd[8], xv[4], xg[8], xh[12];
+      vload<VD_STRIDE>(vme + ov * VD_STRIDE, rec);
 #pragma unroll
-      for (int c = 0; c < 4; ++c) val[c] = vme[ov * 14 + c];
+      for (int c = 0; c < 4; ++c) val[c] = rec[c];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) grd[q] = vme[ov * 14 + 4 + q];
-      const Real r_own = fabs(val[1] * nx + val[2] * ny) * vme[ov * 14 + 12] + vme[ov * 14 + 13];
+      for (int q = 0; q < 8; ++q) grd[q] = rec[4 + q];
+      const Real r_own = fabs(val[1] * nx + val[2] * ny) * rec[12] + rec[13];
       Real r_oth;
       if (cn >= 0) {
         const int xvtx = (jn + 2 - ev) % 3;            // the neighbour's copy of this vertex
+        Real xr[VD_STRIDE];
+        vload<VD_STRIDE>(vnb + xvtx * VD_STRIDE, xr);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) xv[c] = vnb[xvtx * 14 + c];
+        for (int c = 0; c < 4; ++c) xv[c] = xr[c];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) xg[q] = vnb[xvtx * 14 + 4 + q];
+        for (int q = 0; q < 8; ++q) xg[q] = xr[4 + q];
 #pragma unroll
         for (int q = 0; q < 12; ++q) xh[q] = hot[q];
-        r_oth = fabs(xv[1] * nx + xv[2] * ny) * vnb[xvtx * 14 + 12] + vnb[xvtx * 14 + 13];
+        r_oth = fabs(xv[1] * nx + xv[2] * ny) * xr[12] + xr[13];
       } else {
         double px = 0.0, py = 0.0;
         if (cn == -7) { px = m.vxy[(2 * ov) * nt + Kc]; py = m.vxy[(2 * ov + 1) * nt + Kc]; }
@@ -434,18 +442,22 @@ __device__ __forceinline__ void edge_tile(const MeshDev &m, const Phys &ph, cons
           Jq[q][K] += Real(0.5) * (jh[q][0] * jh[q][0] + Real(2) * jh[q][1] * jh[q][1] + jh[q][2] * jh[q][2]);
       }
     }
-    ej[e] = beta;
+    Real er[EJ_STRIDE];
+#pragma unroll
+    for (int r = 0; r < EJ_STRIDE; ++r) er[r] = Real(0);
+    er[0] = beta;
 #pragma unroll
     for (int j = 0; j <= K; ++j) {
-      ej[ej_row(0, j, K) * ne + e] = sqrt(Jq[0][j]);
-      ej[ej_row(3, j, K) * ne + e] = sqrt(Jq[3][j]);
+      er[ej_row(0, j, K)] = sqrt(Jq[0][j]);
+      er[ej_row(3, j, K)] = sqrt(Jq[3][j]);
       if (cw) {
-        ej[ej_row(1, j, K) * ne + e] = sqrt(Jq[1][j]);
-        ej[ej_row(2, j, K) * ne + e] = sqrt(Jq[2][j]);
+        er[ej_row(1, j, K)] = sqrt(Jq[1][j]);
+        er[ej_row(2, j, K)] = sqrt(Jq[2][j]);
       } else {   // RIOE: delta_m = max(delta_mn, delta_mt) -> sqrt(max(J_mn, J_mt))
-        ej[ej_row(1, j, K) * ne + e] = sqrt(fmax(Jq[1][j], Jq[2][j]));
+        er[ej_row(1, j, K)] = sqrt(fmax(Jq[1][j], Jq[2][j]));
       }
     }
+    vstore<EJ_STRIDE>(ej + e * EJ_STRIDE, er);
   }
 }
 
@@ -672,16 +684,19 @@ __device__ __forceinline__ void limit_and_trace_mixed(const MeshDev &m, const Ph
       for (int c = 0; c < 4; ++c) ut[p][c] = float(ud[p][c]);
   }
   // traces, F.n and wave speed at the edge Gauss points for the next stage
+  float amax32 = 0.0f;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
 #pragma unroll
     for (int nu = 0; nu < NQ; ++nu) {
       float f[4];
       const float *u = ut[i * NQ + nu];
-      amax = OpMax()(amax, double(flux_speed(u, nxs[i], nys[i], gm1, gamma, f)));
-      float *o = tr + ((Kc * 3 + i) * NQ + nu) * 8;
+      const float r = flux_speed(u, nxs[i], nys[i], gm1, gamma, f);
+      amax32 = (r > amax32 || r != r) ? r : amax32;
+      float o8[8];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) { o[q] = u[q]; o[4 + q] = f[q]; }
+      for (int q = 0; q < 4; ++q) { o8[q] = u[q]; o8[4 + q] = f[q]; }
+      vstore<8>(tr + ((Kc * 3 + i) * NQ + nu) * 8, o8);
       if (cns[i] <= -3) {
         double qx = 0.0, qy = 0.0;
         if (cns[i] == -7) {
@@ -693,10 +708,12 @@ __device__ __forceinline__ void limit_and_trace_mixed(const MeshDev &m, const Ph
         }
         float up[4];
         ghost_state(-cns[i], u, nxs[i], nys[i], qx, qy, t_out, ph, up);
-        amax = OpMax()(amax, double(wave_speed(up, nxs[i], nys[i], gamma)));
+        const float rg = wave_speed(up, nxs[i], nys[i], gamma);
+        amax32 = (rg > amax32 || rg != rg) ? rg : amax32;
       }
     }
   }
+  amax = OpMax()(amax, double(amax32));
 }
 
 template <int K, typename Real>
@@ -721,8 +738,8 @@ __device__ __forceinline__ void oe_bp_tile(const MeshDev &m, const Phys &ph, Sta
     int32_t cns[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      nxs[i] = Real(m.nrm[(2 * i) * nt + Kc]);
-      nys[i] = Real(m.nrm[(2 * i + 1) * nt + Kc]);
+      nxs[i] = Geo<Real>::nrm(m)[(2 * i) * nt + Kc];
+      nys[i] = Geo<Real>::nrm(m)[(2 * i + 1) * nt + Kc];
       cns[i] = m.conn[i * nt + Kc];
     }
 
@@ -742,18 +759,20 @@ __device__ __forceinline__ void oe_bp_tile(const MeshDev &m, const Phys &ph, Sta
       for (int i = 0; i < 3; ++i) {
         // beta and sqrt of the jump sums of this edge (edge_tile, shared by both cells)
         const int64_t eid = m.cedge[i * nt + Kc];
-        const Real h = Real(m.hgeo[i * nt + Kc]), ih = Real(m.hgeo[(3 + i) * nt + Kc]);
-        const Real bh = ej[eid] * ih;
+        const Real h = Geo<Real>::hgeo(m)[i * nt + Kc], ih = Geo<Real>::hgeo(m)[(3 + i) * nt + Kc];
+        Real er[EJ_STRIDE];
+        vload<EJ_STRIDE>(ej + eid * EJ_STRIDE, er);
+        const Real bh = er[0] * ih;
         // delta_q^j = A^{k,j} h^j sqrt(J) / D_q, A^{k,j} = (2j + 1) / ((2k - 1) j!)
         Real hj = Real(1);
 #pragma unroll
         for (int j = 0; j <= K; ++j) {
           const Real Ah = Real((2.0 * j + 1.0) / ((2.0 * K - 1.0) * (j == 2 ? 2.0 : 1.0))) * hj;
           Real dl[4];
-          dl[0] = Ah * iD[0] * ej[ej_row(0, j, K) * m.ne + eid];
-          dl[1] = Ah * iD[1] * ej[ej_row(1, j, K) * m.ne + eid];
-          dl[2] = cw ? Ah * iD[2] * ej[ej_row(2, j, K) * m.ne + eid] : dl[1];
-          dl[3] = Ah * iD[3] * ej[ej_row(3, j, K) * m.ne + eid];
+          dl[0] = Ah * iD[0] * er[ej_row(0, j, K)];
+          dl[1] = Ah * iD[1] * er[ej_row(1, j, K)];
+          dl[2] = cw ? Ah * iD[2] * er[ej_row(2, j, K)] : dl[1];
+          dl[3] = Ah * iD[3] * er[ej_row(3, j, K)];
 #pragma unroll
           for (int c = 0; c < 4; ++c)
             if (dl[c] != Real(0)) sig[c][j] += bh * dl[c];
@@ -872,9 +891,10 @@ __device__ __forceinline__ void oe_bp_tile(const MeshDev &m, const Phys &ph, Sta
   #pragma unroll
           for (int c = 0; c < 4; ++c) u[c] = Real(a0[c] + (c == 0 ? th_r : th_a) * dev[i * NQ + nu][c]);
           amax = OpMax()(amax, double(flux_speed(u, nxs[i], nys[i], gm1, gamma, f)));
-          Real *o = tr + ((Kc * 3 + i) * NQ + nu) * 8;
+          Real o8[8];
   #pragma unroll
-          for (int q = 0; q < 4; ++q) { o[q] = u[q]; o[4 + q] = f[q]; }
+          for (int q = 0; q < 4; ++q) { o8[q] = u[q]; o8[4 + q] = f[q]; }
+          vstore<8>(tr + ((Kc * 3 + i) * NQ + nu) * 8, o8);
           if (cns[i] < 0 && cns[i] <= -3) {
             double px = 0.0, py = 0.0;
             if (cns[i] == -7) {
