@@ -281,37 +281,105 @@ __device__ __forceinline__ void ghost_state(int tag, const T um[4], T nx, T ny, 
 }
 
 // ------------------------------------------------------------------------
-// Deterministic block reductions (fixed shuffle tree, then warps in order)
+// Deterministic block reductions
 // ------------------------------------------------------------------------
+// Maximum of two non-negative doubles (or +inf, or NaN) on the integer units:
+// for x, y >= +0 the IEEE bit patterns order like the numbers, and a NaN of
+// either sign compares above every number, so it propagates.  A double
+// comparison would occupy GB300's narrow FP64 pipe.
+__device__ __forceinline__ double max_nn(double a, double b) {
+  const unsigned long long x = (unsigned long long)__double_as_longlong(a);
+  const unsigned long long y = (unsigned long long)__double_as_longlong(b);
+  return __longlong_as_double((long long)(x > y ? x : y));
+}
+__device__ __forceinline__ float max_nn(float a, float b) { return (a > b || a != a) ? a : b; }
+
+// x is neither infinite nor NaN, tested on the integer units
+__device__ __forceinline__ bool is_finite_bits(double x) {
+  return (__double_as_longlong(x) & 0x7ff0000000000000LL) != 0x7ff0000000000000LL;
+}
+__device__ __forceinline__ bool is_finite_bits(float x) {
+  return (__float_as_int(x) & 0x7f800000) != 0x7f800000;
+}
+
+// Order-preserving integer key of a double (NaN aside): negative numbers get
+// their magnitude bits flipped, so signed integer comparison orders the keys
+// like the numbers (-0 sorts just below +0).  The map is its own inverse.
+__device__ __forceinline__ long long ord_key(double x) {
+  const long long b = __double_as_longlong(x);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double ord_val(long long k) {
+  return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL));
+}
+
+struct OpSum {
+  template <typename T> __device__ T operator()(T a, T b) const { return a + b; }
+  template <typename T> __device__ static T ident() { return T(0); }
+};
+// NaN-propagating maximum of non-negative values
+struct OpMaxNN {
+  template <typename T> __device__ T operator()(T a, T b) const { return max_nn(a, b); }
+  template <typename T> __device__ static T ident() { return T(0); }
+};
+
+constexpr int pow2_ceil(int n) { return n <= 1 ? 1 : 2 * pow2_ceil((n + 1) / 2); }
+
+// Warp reduction of N values per lane by transposition: at each of the first
+// log2(P) shuffle levels (P = N rounded up to a power of two) a lane keeps half
+// of its values and adds the partner's copies of them, so the level costs half
+// as many operations as the one before; the remaining levels are a butterfly on
+// one value.  Component q ends on lanes q * 32 / P (and their butterfly
+// partners).  The tree is fixed, so the result is reproducible.
 template <int N, typename T, typename Op>
-__device__ __forceinline__ void block_reduce(T v[N], T *out, Op op) {
-  __shared__ T red[TPB / 32][N > 0 ? N : 1];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+__device__ __forceinline__ T warp_reduce_transposed(const T v[N], Op op) {
+  constexpr int P = pow2_ceil(N);
+  static_assert(P <= 32, "too many values for one warp");
+  const int lane = threadIdx.x & 31;
+  T w[P];
 #pragma unroll
-  for (int q = 0; q < N; ++q) {
+  for (int q = 0; q < P; ++q) w[q] = q < N ? v[q] : Op::template ident<T>();
+  int o = 16;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[q] = op(v[q], __shfl_down_sync(0xffffffffu, v[q], o));
-  }
-  if (lane == 0) {
+  for (int cnt = P; cnt > 1; cnt >>= 1, o >>= 1) {
+    const int half = cnt >> 1;
+    const bool up = (lane & o) != 0;
 #pragma unroll
-    for (int q = 0; q < N; ++q) red[warp][q] = v[q];
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int q = 0; q < N; ++q) {
-      T s = red[0][q];
-      for (int w = 1; w < TPB / 32; ++w) s = op(s, red[w][q]);
-      out[q] = s;
+    for (int j = 0; j < half; ++j) {
+      const T send = up ? w[j] : w[j + half];
+      const T keep = up ? w[j + half] : w[j];
+      w[j] = op(keep, __shfl_xor_sync(0xffffffffu, send, o));
     }
   }
-  __syncthreads();   // red[] may be reused by the next call of this block
+#pragma unroll
+  for (; o > 0; o >>= 1) w[0] = op(w[0], __shfl_xor_sync(0xffffffffu, w[0], o));
+  return w[0];
+}
+
+// Block reduction: transposed warp reduction, then the warps in order.  Ends
+// with a barrier, so the block may call it again at once.
+template <int N, typename T, typename U, typename Op>
+__device__ __forceinline__ void block_reduce(const T v[N], U *out, Op op) {
+  constexpr int P = pow2_ceil(N);
+  __shared__ T red[TPB / 32][N > 0 ? N : 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const T r = warp_reduce_transposed<N, T, Op>(v, op);
+  if (lane % (32 / P) == 0 && lane / (32 / P) < N) red[warp][lane / (32 / P)] = r;
+  __syncthreads();
+  if (threadIdx.x < N) {
+    T s = red[0][threadIdx.x];
+#pragma unroll
+    for (int w = 1; w < TPB / 32; ++w) s = op(s, red[w][threadIdx.x]);
+    out[threadIdx.x] = U(s);
+  }
+  __syncthreads();
 }
 
 // Fixed-order reduction of nblk partials of N values by one block: FIN_THREADS
 // virtual lanes each reduce a strided subset, then a fixed tree.  The
 // arithmetic does not depend on the block size, so a persistent kernel with
-// TPB threads reproduces the FIN_THREADS-thread finalize kernels bitwise.
+// TPB threads reproduces the FIN_THREADS-thread finalize kernels bitwise.  The
+// strided loop loads four partials ahead of the operations, in the same order.
 template <int N, typename T, typename Op>
 __device__ void fin_reduce(const T *part, int nblk, T init, Op op, T out[N]) {
   __shared__ T sh[FIN_THREADS][N];
@@ -319,9 +387,21 @@ __device__ void fin_reduce(const T *part, int nblk, T init, Op op, T out[N]) {
     T acc[N];
 #pragma unroll
     for (int q = 0; q < N; ++q) acc[q] = init;
-    for (int b = vt; b < nblk; b += FIN_THREADS)
+    int b = vt;
+    for (; b + 3 * FIN_THREADS < nblk; b += 4 * FIN_THREADS) {
+      T x[4][N];
 #pragma unroll
-      for (int q = 0; q < N; ++q) acc[q] = op(acc[q], part[b * N + q]);
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int q = 0; q < N; ++q) x[u][q] = part[(int64_t)(b + u * FIN_THREADS) * N + q];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int q = 0; q < N; ++q) acc[q] = op(acc[q], x[u][q]);
+    }
+    for (; b < nblk; b += FIN_THREADS)
+#pragma unroll
+      for (int q = 0; q < N; ++q) acc[q] = op(acc[q], part[(int64_t)b * N + q]);
 #pragma unroll
     for (int q = 0; q < N; ++q) sh[vt][q] = acc[q];
   }
@@ -336,11 +416,6 @@ __device__ void fin_reduce(const T *part, int nblk, T init, Op op, T out[N]) {
   for (int q = 0; q < N; ++q) out[q] = sh[0][q];
   __syncthreads();
 }
-
-struct OpSum { template <typename T> __device__ T operator()(T a, T b) const { return a + b; } };
-struct OpMax {
-  __device__ double operator()(double a, double b) const { return (a > b || a != a) ? a : b; }
-};
 
 // ------------------------------------------------------------------------
 // Per-solve finalize steps (one block; thread 0 writes the scalars)
@@ -373,7 +448,7 @@ __device__ __forceinline__ void fin_mean_block(const double *part, int nblk, Sca
 // sup deviations, then the reciprocal OE normalisers
 __device__ __forceinline__ void fin_dev_block(const double *part, int nblk, Scalars *sc, int cw) {
   double r[5];
-  fin_reduce<5>(part, nblk, 0.0, OpMax(), r);
+  fin_reduce<5>(part, nblk, 0.0, OpMaxNN(), r);
   if (threadIdx.x == 0) {
     for (int q = 0; q < 5; ++q) sc->dev[q] = r[q];
     write_inv_normalisers(sc, cw);
@@ -384,7 +459,7 @@ __device__ __forceinline__ void fin_dev_block(const double *part, int nblk, Scal
 __device__ __forceinline__ void fin_alpha_block(const double *pa, const long long *pc, int nblk, Scalars *sc,
                                                 int stage) {
   double a[1];
-  fin_reduce<1>(pa, nblk, 0.0, OpMax(), a);
+  fin_reduce<1>(pa, nblk, 0.0, OpMaxNN(), a);
   long long c[2];
   fin_reduce<2>(pc, nblk, 0LL, OpSum(), c);
   if (threadIdx.x == 0) {

@@ -6,7 +6,10 @@
 
 namespace dg {
 
-struct OpMinD { __device__ double operator()(double a, double b) const { return a < b ? a : b; } };
+struct OpMinD {
+  __device__ double operator()(double a, double b) const { return a < b ? a : b; }
+  template <typename T> __device__ static T ident() { return T(INFINITY); }
+};
 
 // ==========================================================================
 // Geometry and optimal convex decomposition (Sec. 4.2, eqs. 1040, 1139;

@@ -109,12 +109,12 @@ __global__ void __launch_bounds__(TPB) k_na_dev(int64_t nt, const double *__rest
       d[4] = fmax(d[4], fabs(v[2]));
     }
   }
-  block_reduce<5>(d, scratch + NA_OFF_DEV + 5 * blockIdx.x, OpMax());
+  block_reduce<5>(d, scratch + NA_OFF_DEV + 5 * blockIdx.x, OpMaxNN());
 }
 
 __global__ void k_na_fin(int nblk, double area_total, double *scratch, double *out) {
   double r[5];
-  na_fin_reduce<5>(scratch + NA_OFF_DEV, nblk, 0.0, OpMax(), r);
+  na_fin_reduce<5>(scratch + NA_OFF_DEV, nblk, 0.0, OpMaxNN(), r);
   if (threadIdx.x == 0) {
     for (int c = 0; c < 4; ++c) out[c] = scratch[NA_OFF_MEAN + c];
     out[4] = r[0];

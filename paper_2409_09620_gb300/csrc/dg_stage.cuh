@@ -15,6 +15,16 @@
 
 namespace dg {
 
+#ifndef RK_MINB_F
+#define RK_MINB_F 3
+#endif
+#ifndef STATS_MINB_F
+#define STATS_MINB_F 4
+#endif
+#ifndef OEBP_MINB_F
+#define OEBP_MINB_F 3
+#endif
+
 template <typename Real, int NB>
 __device__ __forceinline__ void load_state(const StateDev<Real> &s, int64_t nt, int64_t K, double avg[4],
                                            Real hi[4][NB]) {
@@ -233,7 +243,7 @@ __device__ __forceinline__ void rk_tile(const MeshDev &m, const Phys &ph, StateD
 }
 
 template <int K, typename Real>
-__global__ void __launch_bounds__(TPB) k_rk(MeshDev m, Phys ph, StateDev<Real> v, StateDev<Real> un,
+__global__ void __launch_bounds__(TPB, sizeof(Real) == 4 ? RK_MINB_F : 1) k_rk(MeshDev m, Phys ph, StateDev<Real> v, StateDev<Real> un,
                                             StateDev<Real> uh, const Real *__restrict__ tr,
                                             Real *__restrict__ vdo, Real *__restrict__ hso,
                                             double *__restrict__ part_sum, const Scalars *__restrict__ sc,
@@ -251,7 +261,8 @@ __device__ __forceinline__ void stats_tile(const MeshDev &m, StateDev<Real> uh, 
   constexpr int NB = Deg<K>::NB, NV = Deg<K>::NV;
   const int64_t nt = m.nt;
   const int64_t Kc = tile * TPB + threadIdx.x;
-  double d[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  // deviations in the working precision, reduced in it; one conversion per block
+  Real dr[5] = {Real(0), Real(0), Real(0), Real(0), Real(0)};
   if (Kc < nt) {
     double a0[4];
     Real hi[4][NB];
@@ -259,22 +270,18 @@ __device__ __forceinline__ void stats_tile(const MeshDev &m, StateDev<Real> uh, 
     double off[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) off[c] = a0[c] - sc->mean[c];   // deviation of the cell mean
-    // deviations in the working precision; one conversion per cell
-    Real dr[5] = {Real(0), Real(0), Real(0), Real(0), Real(0)};
 #pragma unroll
     for (int mu = 0; mu < NV; ++mu) {
       Real u[4];
       eval_fixed<Real, NB>(off, hi, vol_xi(NV, mu), vol_eta(NV, mu), u);
-      dr[0] = fmax(dr[0], fabs(u[0]));
-      dr[1] = fmax(dr[1], sqrt(u[1] * u[1] + u[2] * u[2]));
-      dr[2] = fmax(dr[2], fabs(u[3]));
-      dr[3] = fmax(dr[3], fabs(u[1]));
-      dr[4] = fmax(dr[4], fabs(u[2]));
+      dr[0] = max_nn(dr[0], fabs(u[0]));
+      dr[1] = max_nn(dr[1], sqrt(u[1] * u[1] + u[2] * u[2]));
+      dr[2] = max_nn(dr[2], fabs(u[3]));
+      dr[3] = max_nn(dr[3], fabs(u[1]));
+      dr[4] = max_nn(dr[4], fabs(u[2]));
     }
-#pragma unroll
-    for (int q = 0; q < 5; ++q) d[q] = double(dr[q]);
   }
-  block_reduce<5>(d, part_dev + 5 * tile, OpMax());
+  block_reduce<5>(dr, part_dev + 5 * tile, OpMaxNN());
 }
 
 
@@ -410,7 +417,7 @@ __device__ __forceinline__ void edge_tile(const MeshDev &m, const Phys &ph, cons
         // a mirror or copied state has the same spectral radius
         r_oth = cn >= -2 ? r_own : wave_speed(xv, nx, ny, gamma);
       }
-      beta = fmax(beta, fmax(r_own, r_oth));
+      beta = max_nn(beta, max_nn(r_own, r_oth));
       Real jv[4], jg[4][2], jh[4][3];
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
@@ -454,7 +461,7 @@ __device__ __forceinline__ void edge_tile(const MeshDev &m, const Phys &ph, cons
         er[ej_row(1, j, K)] = sqrt(Jq[1][j]);
         er[ej_row(2, j, K)] = sqrt(Jq[2][j]);
       } else {   // RIOE: delta_m = max(delta_mn, delta_mt) -> sqrt(max(J_mn, J_mt))
-        er[ej_row(1, j, K)] = sqrt(fmax(Jq[1][j], Jq[2][j]));
+        er[ej_row(1, j, K)] = sqrt(max_nn(Jq[1][j], Jq[2][j]));
       }
     }
     vstore<EJ_STRIDE>(ej + e * EJ_STRIDE, er);
@@ -713,7 +720,7 @@ __device__ __forceinline__ void limit_and_trace_mixed(const MeshDev &m, const Ph
       }
     }
   }
-  amax = OpMax()(amax, double(amax32));
+  amax = max_nn(amax, double(amax32));
 }
 
 template <int K, typename Real>
@@ -763,6 +770,9 @@ __device__ __forceinline__ void oe_bp_tile(const MeshDev &m, const Phys &ph, Sta
         Real er[EJ_STRIDE];
         vload<EJ_STRIDE>(ej + eid * EJ_STRIDE, er);
         const Real bh = er[0] * ih;
+        // a zero delta adds nothing; it is skipped only when beta / h is not
+        // finite (beta = +inf at a vertex with rho <= 0), where 0 * inf would be NaN
+        const bool bh_finite = is_finite_bits(bh);
         // delta_q^j = A^{k,j} h^j sqrt(J) / D_q, A^{k,j} = (2j + 1) / ((2k - 1) j!)
         Real hj = Real(1);
 #pragma unroll
@@ -775,7 +785,7 @@ __device__ __forceinline__ void oe_bp_tile(const MeshDev &m, const Phys &ph, Sta
           dl[3] = Ah * iD[3] * er[ej_row(3, j, K)];
 #pragma unroll
           for (int c = 0; c < 4; ++c)
-            if (dl[c] != Real(0)) sig[c][j] += bh * dl[c];
+            if (bh_finite || dl[c] != Real(0)) sig[c][j] += bh * dl[c];
           hj *= h;
         }
       }
@@ -845,9 +855,11 @@ __device__ __forceinline__ void oe_bp_tile(const MeshDev &m, const Phys &ph, Sta
           cnt[1] = 1;
         } else {
           // Step 1: density
-          double rmin = a0[0] + dev[0][0];
+          // minimum on the integer units through order-preserving keys
+          long long kmin = ord_key(a0[0] + dev[0][0]);
   #pragma unroll
-          for (int p = 1; p < NE + 2; ++p) rmin = fmin(rmin, a0[0] + dev[p][0]);
+          for (int p = 1; p < NE + 2; ++p) kmin = min(kmin, ord_key(a0[0] + dev[p][0]));
+          const double rmin = ord_val(kmin);
           const double eps1 = fmin(a0[0], 1e-13);
           double th1 = 1.0;
           if (rmin < eps1) th1 = (a0[0] - eps1) / (a0[0] - rmin);
@@ -890,7 +902,7 @@ __device__ __forceinline__ void oe_bp_tile(const MeshDev &m, const Phys &ph, Sta
           Real u[4], f[4];
   #pragma unroll
           for (int c = 0; c < 4; ++c) u[c] = Real(a0[c] + (c == 0 ? th_r : th_a) * dev[i * NQ + nu][c]);
-          amax = OpMax()(amax, double(flux_speed(u, nxs[i], nys[i], gm1, gamma, f)));
+          amax = max_nn(amax, double(flux_speed(u, nxs[i], nys[i], gm1, gamma, f)));
           Real o8[8];
   #pragma unroll
           for (int q = 0; q < 4; ++q) { o8[q] = u[q]; o8[4 + q] = f[q]; }
@@ -906,7 +918,7 @@ __device__ __forceinline__ void oe_bp_tile(const MeshDev &m, const Phys &ph, Sta
             }
             Real up[4];
             ghost_state(-cns[i], u, nxs[i], nys[i], px, py, t_out, ph, up);
-            amax = OpMax()(amax, double(wave_speed(up, nxs[i], nys[i], gamma)));
+            amax = max_nn(amax, double(wave_speed(up, nxs[i], nys[i], gamma)));
           }
         }
       }
@@ -915,7 +927,7 @@ __device__ __forceinline__ void oe_bp_tile(const MeshDev &m, const Phys &ph, Sta
     }
   }
   double av[1] = {amax};
-  block_reduce<1>(av, part_alpha + tile, OpMax());
+  block_reduce<1>(av, part_alpha + tile, OpMaxNN());
   __syncthreads();
   long long cv[2] = {cnt[0], cnt[1]};
   block_reduce<2>(cv, part_cnt + 2 * tile, OpSum());
@@ -924,7 +936,7 @@ __device__ __forceinline__ void oe_bp_tile(const MeshDev &m, const Phys &ph, Sta
 
 // OE statistics of the tile's cells and the jump data of the edges it owns
 template <int K, typename Real>
-__global__ void __launch_bounds__(TPB) k_stats(MeshDev m, Phys ph, StateDev<Real> uh, double *__restrict__ part_dev,
+__global__ void __launch_bounds__(TPB, sizeof(Real) == 4 ? STATS_MINB_F : 1) k_stats(MeshDev m, Phys ph, StateDev<Real> uh, double *__restrict__ part_dev,
                                                const Real *__restrict__ vdi, const Real *__restrict__ hsi,
                                                Real *__restrict__ ej, const Scalars *__restrict__ sc, double c_out) {
   if (!sc->active) return;
@@ -934,7 +946,7 @@ __global__ void __launch_bounds__(TPB) k_stats(MeshDev m, Phys ph, StateDev<Real
 
 // the FP32 form is latency-bound: ask for three resident blocks per SM
 template <int K, typename Real>
-__global__ void __launch_bounds__(TPB, sizeof(Real) == 4 ? 3 : 1) k_oe_bp(MeshDev m, Phys ph, StateDev<Real> uh,
+__global__ void __launch_bounds__(TPB, sizeof(Real) == 4 ? OEBP_MINB_F : 1) k_oe_bp(MeshDev m, Phys ph, StateDev<Real> uh,
                                                                         StateDev<Real> out,
                                                const Real *__restrict__ ej, Real *__restrict__ tr,
                                                double *__restrict__ part_alpha, long long *__restrict__ part_cnt,
