@@ -22,7 +22,7 @@
 namespace dg {
 
 constexpr int TPB = 128;                 // cells per block
-constexpr int FIN_THREADS = 256;         // threads of the finalize kernels
+constexpr int FIN_THREADS = 1024;        // threads (virtual lanes) of the finalize reductions
 
 template <int K> struct Deg;
 template <> struct Deg<1> { static constexpr int NB = 3, NQ = 2, NV = 3; };
@@ -380,9 +380,18 @@ __device__ __forceinline__ void block_reduce(const T v[N], U *out, Op op) {
 // arithmetic does not depend on the block size, so a persistent kernel with
 // TPB threads reproduces the FIN_THREADS-thread finalize kernels bitwise.  The
 // strided loop loads four partials ahead of the operations, in the same order.
+// Shared scratch of fin_reduce: one array per kernel, whatever the value type
+// and count, so a kernel that reduces several kinds of partials stays within
+// the static shared-memory limit.
+__device__ __forceinline__ unsigned char *fin_scratch() {
+  __shared__ __align__(16) unsigned char buf[FIN_THREADS * 5 * sizeof(double)];
+  return buf;
+}
+
 template <int N, typename T, typename Op>
 __device__ void fin_reduce(const T *part, int nblk, T init, Op op, T out[N]) {
-  __shared__ T sh[FIN_THREADS][N];
+  static_assert(N * sizeof(T) <= 5 * sizeof(double), "fin_scratch too small");
+  T (*sh)[N] = reinterpret_cast<T (*)[N]>(fin_scratch());
   for (int vt = threadIdx.x; vt < FIN_THREADS; vt += blockDim.x) {
     T acc[N];
 #pragma unroll

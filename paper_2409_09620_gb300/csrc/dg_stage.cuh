@@ -15,14 +15,26 @@
 
 namespace dg {
 
+// Resident blocks per SM requested from the register allocator (FP32 / FP64
+// instantiations).  Higher occupancy hides the latency of the neighbour
+// gathers and of the FP64 pipe better than the few spilled registers cost.
 #ifndef RK_MINB_F
-#define RK_MINB_F 3
+#define RK_MINB_F 5
 #endif
 #ifndef STATS_MINB_F
-#define STATS_MINB_F 4
+#define STATS_MINB_F 6
 #endif
 #ifndef OEBP_MINB_F
-#define OEBP_MINB_F 3
+#define OEBP_MINB_F 4
+#endif
+#ifndef RK_MINB_D
+#define RK_MINB_D 3
+#endif
+#ifndef STATS_MINB_D
+#define STATS_MINB_D 3
+#endif
+#ifndef OEBP_MINB_D
+#define OEBP_MINB_D 3
 #endif
 
 template <typename Real, int NB>
@@ -243,7 +255,7 @@ __device__ __forceinline__ void rk_tile(const MeshDev &m, const Phys &ph, StateD
 }
 
 template <int K, typename Real>
-__global__ void __launch_bounds__(TPB, sizeof(Real) == 4 ? RK_MINB_F : 1) k_rk(MeshDev m, Phys ph, StateDev<Real> v, StateDev<Real> un,
+__global__ void __launch_bounds__(TPB, sizeof(Real) == 4 ? RK_MINB_F : RK_MINB_D) k_rk(MeshDev m, Phys ph, StateDev<Real> v, StateDev<Real> un,
                                             StateDev<Real> uh, const Real *__restrict__ tr,
                                             Real *__restrict__ vdo, Real *__restrict__ hso,
                                             double *__restrict__ part_sum, const Scalars *__restrict__ sc,
@@ -936,7 +948,7 @@ __device__ __forceinline__ void oe_bp_tile(const MeshDev &m, const Phys &ph, Sta
 
 // OE statistics of the tile's cells and the jump data of the edges it owns
 template <int K, typename Real>
-__global__ void __launch_bounds__(TPB, sizeof(Real) == 4 ? STATS_MINB_F : 1) k_stats(MeshDev m, Phys ph, StateDev<Real> uh, double *__restrict__ part_dev,
+__global__ void __launch_bounds__(TPB, sizeof(Real) == 4 ? STATS_MINB_F : STATS_MINB_D) k_stats(MeshDev m, Phys ph, StateDev<Real> uh, double *__restrict__ part_dev,
                                                const Real *__restrict__ vdi, const Real *__restrict__ hsi,
                                                Real *__restrict__ ej, const Scalars *__restrict__ sc, double c_out) {
   if (!sc->active) return;
@@ -946,7 +958,7 @@ __global__ void __launch_bounds__(TPB, sizeof(Real) == 4 ? STATS_MINB_F : 1) k_s
 
 // the FP32 form is latency-bound: ask for three resident blocks per SM
 template <int K, typename Real>
-__global__ void __launch_bounds__(TPB, sizeof(Real) == 4 ? OEBP_MINB_F : 1) k_oe_bp(MeshDev m, Phys ph, StateDev<Real> uh,
+__global__ void __launch_bounds__(TPB, sizeof(Real) == 4 ? OEBP_MINB_F : OEBP_MINB_D) k_oe_bp(MeshDev m, Phys ph, StateDev<Real> uh,
                                                                         StateDev<Real> out,
                                                const Real *__restrict__ ej, Real *__restrict__ tr,
                                                double *__restrict__ part_alpha, long long *__restrict__ part_cnt,
