@@ -161,8 +161,9 @@ int32_t dg_set_state(dg_solver *solver, const double *coeffs, double t);
  * set by the last dg_advance call; use dg_advance_async-style open-ended runs
  * for timing).  ms[q] and launches[q] receive the summed duration and launch
  * count of kernel kind q: 0 step_begin (dt), 1 rk (volume + edge flux + RK
- * combine), 2 fin_mean, 3 stats (OE normalisers), 4 fin_dev, 5 oe_bp (RIOE +
- * limiter + traces), 6 fin_alpha. */
+ * combine), 2 fin_mean (domain means), 3 stats (deviation maxima and edge OE
+ * records), 4 fin_dev (normalisers), 5 oe_bp (RIOE + limiter + traces), 6
+ * fin_alpha (alpha, counters, time).  A step is 19 launches (13 with OE off). */
 #define DG_NUM_KERNEL_KINDS 7
 int32_t dg_profile_steps(dg_solver *solver, int64_t n, double *ms, int64_t *launches);
 /* the solver's CUDA stream (cudaStream_t) */

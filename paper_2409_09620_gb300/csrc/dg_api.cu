@@ -80,6 +80,7 @@ struct dg_solver {
   void *tr = nullptr, *vd = nullptr, *hs = nullptr, *ej = nullptr;
   double *part_sum = nullptr, *part_dev = nullptr, *part_alpha = nullptr;
   long long *part_cnt = nullptr;
+  FinBufs fin{};
   Scalars *sc = nullptr;
   cudaGraphExec_t step_exec = nullptr;
   StageCtx ctx{};
@@ -89,6 +90,7 @@ struct dg_solver {
     for (auto *b : bufs) { cudaFree(b->avg); cudaFree(b->hi); }
     cudaFree(tr); cudaFree(vd); cudaFree(hs); cudaFree(ej);
     cudaFree(part_sum); cudaFree(part_dev); cudaFree(part_alpha); cudaFree(part_cnt); cudaFree(sc);
+    cudaFree(fin.grp_sum); cudaFree(fin.grp_dev); cudaFree(fin.grp_alpha); cudaFree(fin.grp_cnt); cudaFree(fin.tick);
     if (own_stream && stream) cudaStreamDestroy(stream);
   }
 };
@@ -497,6 +499,13 @@ extern "C" int32_t dg_init(const dg_mesh *mesh, const dg_config *cfg, const doub
   STRY(dalloc(&s->part_dev, 5 * nblk));
   STRY(dalloc(&s->part_alpha, nblk));
   STRY(dalloc(&s->part_cnt, 2 * nblk));
+  const int64_t ngrp = num_groups(nblk);
+  STRY(dalloc(&s->fin.grp_sum, 4 * ngrp));
+  STRY(dalloc(&s->fin.grp_dev, 5 * ngrp));
+  STRY(dalloc(&s->fin.grp_alpha, ngrp));
+  STRY(dalloc(&s->fin.grp_cnt, 2 * ngrp));
+  STRY(dalloc(&s->fin.tick, 3 * ticket_slots(nblk)));
+  STRY(cudaMemsetAsync(s->fin.tick, 0, 3 * ticket_slots(nblk) * sizeof(unsigned), s->stream));   // tickets start at zero
   STRY(dalloc(&s->sc, 1));
   // context of every stage launch
   StageCtx &c = s->ctx;
@@ -530,6 +539,7 @@ extern "C" int32_t dg_init(const dg_mesh *mesh, const dg_config *cfg, const doub
   c.part_dev = s->part_dev;
   c.part_alpha = s->part_alpha;
   c.part_cnt = s->part_cnt;
+  c.fin = s->fin;
   c.sc = s->sc;
   // scalars
   Scalars h{};
@@ -764,7 +774,7 @@ extern "C" int32_t dg_op_oe(dg_solver *s, const double *u, double dt, const doub
   h.t = t;
   h.dt = dt;
   if ((rc = write_scalars(s, &h)) != DG_OK) return rc;
-  launch_stats_only(s->ctx, s->uh, 0.0);                    // jump data of every edge at time t
+  launch_stats(s->ctx, s->uh, 0.0);                         // jump data of every edge at time t
   CUDA_TRY(cudaGetLastError());
   if ((rc = read_scalars(s, &h)) != DG_OK) return rc;
   for (int c = 0; c < 4; ++c) h.mean[c] = stats[c];

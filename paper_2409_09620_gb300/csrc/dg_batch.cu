@@ -1,7 +1,10 @@
 // dg_batch.cu -- many independent solves advanced together: one persistent
 // (cooperative) launch per SSP-RK3 stage covers every solve.  Each launch runs
-// the phases of a stage (flux, means, OE normalisers, RIOE + limiter, alpha)
-// over a work list of (solve, tile range) chunks, separated by grid barriers.
+// the three phases of a stage (flux + means; deviations, edge records and OE
+// normalisers; RIOE + limiter + alpha) over a work list of (solve, tile range)
+// chunks, separated by grid barriers.  Each phase finalises its reductions in
+// the block that completes them, in the same fixed order as the per-solve
+// kernels.
 //
 // Every solve keeps its own buffers, scalars (t, dt, alpha, normalisers) and
 // per-tile partials; tiles never straddle solves and partials are per TPB
@@ -27,6 +30,7 @@ struct SolveDev {
   void *tr, *vd, *hs, *ej;
   double *part_sum, *part_dev, *part_alpha;
   long long *part_cnt;
+  FinBufs fin;
   Scalars *sc;
   int k, oe, bp, pad;
   int64_t ntiles;
@@ -101,7 +105,7 @@ __global__ void __launch_bounds__(TPB) k_batch_stage(const SolveDev *__restrict_
       for (int i = blockIdx.x; i < nsv; i += gridDim.x) step_begin_thread(sv[i].sc);
     if (!grid_sync(bar, nb)) return;
   }
-  // phase 1: volume + edge fluxes + RK combination
+  // phase 1: volume + edge fluxes + RK combination; domain means
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
     const WorkItem it = work[w];
     const SolveDev &S = sv[it.solve];
@@ -114,14 +118,11 @@ __global__ void __launch_bounds__(TPB) k_batch_stage(const SolveDev *__restrict_
       else
         rk_tile<2, Real>(S.mesh, S.ph, v, un, uh, (const Real *)S.tr, (Real *)S.vd, (Real *)S.hs, S.part_sum, S.sc,
                          a, b, c_in, t);
+      finish_means(S.part_sum, S.fin, t, S.ntiles, S.sc);
     }
   }
   if (!grid_sync(bar, nb)) return;
-  // phase 2: domain means
-  for (int i = blockIdx.x; i < nsv; i += gridDim.x)
-    if (sv[i].sc->active) fin_mean_block(sv[i].part_sum, (int)sv[i].ntiles, sv[i].sc);
-  if (!grid_sync(bar, nb)) return;
-  // phase 3: sup deviations at the volume points (OE normalisers)
+  // phase 2: sup deviations at the volume points, edge OE records; normalisers
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
     const WorkItem it = work[w];
     const SolveDev &S = sv[it.solve];
@@ -135,13 +136,11 @@ __global__ void __launch_bounds__(TPB) k_batch_stage(const SolveDev *__restrict_
         stats_tile<2, Real>(S.mesh, uh, S.part_dev, S.sc, t);
         edge_tile<2, Real>(S.mesh, S.ph, (const Real *)S.vd, (const Real *)S.hs, (Real *)S.ej, S.sc, c_out, t);
       }
+      finish_deviations(S.part_dev, S.fin, t, S.ntiles, S.sc, S.oe == 2);
     }
   }
   if (!grid_sync(bar, nb)) return;
-  for (int i = blockIdx.x; i < nsv; i += gridDim.x)
-    if (sv[i].sc->active && sv[i].oe) fin_dev_block(sv[i].part_dev, (int)sv[i].ntiles, sv[i].sc, sv[i].oe == 2);
-  if (!grid_sync(bar, nb)) return;
-  // phase 5: RIOE + BP limiter + traces and alpha of the stage result
+  // phase 3: RIOE + BP limiter + traces; alpha of the stage result, time update
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
     const WorkItem it = work[w];
     const SolveDev &S = sv[it.solve];
@@ -154,12 +153,9 @@ __global__ void __launch_bounds__(TPB) k_batch_stage(const SolveDev *__restrict_
       else
         oe_bp_tile<2, Real>(S.mesh, S.ph, uh, out, (const Real *)S.ej, (Real *)S.tr, S.part_alpha, S.part_cnt,
                             S.sc, S.oe != 0, S.bp != 0, c_out, t);
+      finish_alpha(S.part_alpha, S.part_cnt, S.fin, t, S.ntiles, S.sc, stage);
     }
   }
-  if (!grid_sync(bar, nb)) return;
-  // phase 6: alpha of the next stage input; time update after the last stage
-  for (int i = blockIdx.x; i < nsv; i += gridDim.x)
-    if (sv[i].sc->active) fin_alpha_block(sv[i].part_alpha, sv[i].part_cnt, (int)sv[i].ntiles, sv[i].sc, stage);
 }
 
 }  // namespace dg
@@ -238,6 +234,7 @@ struct BatchCore {
       d.avg[2] = us.avg; d.hi[2] = us.hi;
       d.tr = c.tr; d.vd = c.vd; d.hs = c.hs; d.ej = c.ej;
       d.part_sum = c.part_sum; d.part_dev = c.part_dev; d.part_alpha = c.part_alpha; d.part_cnt = c.part_cnt;
+      d.fin = c.fin;
       d.sc = c.sc;
       d.k = c.k;
       d.oe = c.phys.oe;
@@ -317,6 +314,9 @@ struct BatchCore {
     if (h.error) {
       BarrierState z{};
       cudaMemcpy(d_bar, &z, sizeof(z), cudaMemcpyHostToDevice);
+      // blocks that left early may hold finalisation tickets: clear them
+      for (const SolveDev &d : host_sv)
+        cudaMemset(d.fin.tick, 0, 3 * ticket_slots(d.ntiles) * sizeof(unsigned));
       return set_error(DG_ETIMEOUT, "a grid barrier of the batch kernel timed out");
     }
     return DG_OK;

@@ -446,31 +446,124 @@ __device__ __forceinline__ void write_inv_normalisers(Scalars *sc, int cw) {
   }
 }
 
-// domain means of u_h from the block sums of |K| u_h^(0)
-__device__ __forceinline__ void fin_mean_block(const double *part, int nblk, Scalars *sc) {
+// ------------------------------------------------------------------------
+// Finalisation inside the producing kernel, in a fixed order
+// ------------------------------------------------------------------------
+// The tiles of a reduction (TPB cells each, one partial per tile) form groups
+// of TILE_GROUP consecutive tiles.  After writing its partial, a block takes a
+// ticket for its group; the block that takes the group's last ticket reduces
+// the group's partials with block_reduce and takes a ticket at the top level;
+// the block that takes the last top-level ticket reduces the group results in
+// chunks of TPB, in order, and writes the scalars.  The arithmetic depends only
+// on the number of tiles, not on which block finishes when, so results are
+// reproducible and the same in the per-solve kernels and the batch kernel.
+// Every ticket counter is reset by the block that takes its last ticket, so it
+// is zero again when the next launch (or batch phase) starts.
+constexpr int TILE_GROUP = TPB;
+__host__ __device__ __forceinline__ int64_t num_groups(int64_t ntiles) {
+  return (ntiles + TILE_GROUP - 1) / TILE_GROUP;
+}
+// ticket counters of one reduction: one per group, then the top level
+__host__ __device__ __forceinline__ int64_t ticket_slots(int64_t ntiles) { return num_groups(ntiles) + 1; }
+
+// Called by every thread of the block once the block's results are written:
+// true in the block that took the last of `total` tickets of *cnt.
+// The block's writes are ordered before the ticket by the barrier and one
+// device-scope fence of thread 0 (cumulative over what the barrier ordered);
+// the last block fences again before its threads read the other blocks'
+// results.
+__device__ __forceinline__ bool take_ticket(unsigned *cnt, unsigned total) {
+  __shared__ int s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned t = atomicAdd(cnt, 1u);
+    const int last = t + 1 == total;
+    if (last) {
+      atomicExch(cnt, 0u);               // every ticket is taken: reset for the next round
+      __threadfence();
+    }
+    s_last = last;
+  }
+  __syncthreads();
+  const bool last = s_last != 0;
+  __syncthreads();                       // s_last may be rewritten by the next call
+  return last;
+}
+
+// partials of other blocks are read from L2 (L1 is not coherent across SMs)
+__device__ __forceinline__ double ld_l2(const double *p) { return __ldcg(p); }
+__device__ __forceinline__ long long ld_l2(const long long *p) { return __ldcg(p); }
+
+// group g's partials -> grp[g]
+template <int N, typename T, typename Op>
+__device__ __forceinline__ void reduce_group(const T *part, int64_t g, int64_t ntiles, T *grp, Op op) {
+  const int64_t t0 = g * TILE_GROUP;
+  const int64_t n = ntiles - t0 < TILE_GROUP ? ntiles - t0 : TILE_GROUP;
+  T v[N];
+#pragma unroll
+  for (int q = 0; q < N; ++q)
+    v[q] = threadIdx.x < n ? ld_l2(part + (t0 + threadIdx.x) * N + q) : Op::template ident<T>();
+  block_reduce<N>(v, grp + g * N, op);
+}
+
+// all group results, in chunks of TPB -> out[] in every thread
+template <int N, typename T, typename Op>
+__device__ __forceinline__ void reduce_top(const T *grp, int64_t ng, Op op, T out[N]) {
+  __shared__ T res[N];
+#pragma unroll
+  for (int q = 0; q < N; ++q) out[q] = Op::template ident<T>();
+  for (int64_t c0 = 0; c0 < ng; c0 += TPB) {
+    T v[N];
+#pragma unroll
+    for (int q = 0; q < N; ++q)
+      v[q] = c0 + threadIdx.x < ng ? ld_l2(grp + (c0 + threadIdx.x) * N + q) : Op::template ident<T>();
+    block_reduce<N>(v, res, op);
+#pragma unroll
+    for (int q = 0; q < N; ++q) out[q] = op(out[q], res[q]);
+    __syncthreads();
+  }
+}
+
+// scratch of the in-kernel finalisation of one solve
+struct FinBufs {
+  double *grp_sum, *grp_dev, *grp_alpha;   // [ng][4], [ng][5], [ng]
+  long long *grp_cnt;                      // [ng][2]
+  unsigned *tick;                          // 3 reductions x ticket_slots(ntiles)
+};
+
+// Top level of each finalisation: the block that takes the last top-level
+// ticket reduces the group results and writes the scalars.  The three kinds
+// use consecutive ranges of ticket_slots(ntiles) counters.
+__device__ __forceinline__ void finish_means_top(const FinBufs &f, int64_t ntiles, Scalars *sc) {
+  const int64_t ng = num_groups(ntiles);
+  if (!take_ticket(f.tick + ng, (unsigned)ng)) return;
   double r[4];
-  fin_reduce<4>(part, nblk, 0.0, OpSum(), r);
+  reduce_top<4>(f.grp_sum, ng, OpSum(), r);
   if (threadIdx.x == 0)
     for (int c = 0; c < 4; ++c) sc->mean[c] = r[c] / sc->area_total;
 }
 
-// sup deviations, then the reciprocal OE normalisers
-__device__ __forceinline__ void fin_dev_block(const double *part, int nblk, Scalars *sc, int cw) {
+__device__ __forceinline__ void finish_deviations_top(const FinBufs &f, int64_t ntiles, Scalars *sc, int cw) {
+  const int64_t ng = num_groups(ntiles);
+  if (!take_ticket(f.tick + ticket_slots(ntiles) + ng, (unsigned)ng)) return;
   double r[5];
-  fin_reduce<5>(part, nblk, 0.0, OpMaxNN(), r);
+  reduce_top<5>(f.grp_dev, ng, OpMaxNN(), r);
   if (threadIdx.x == 0) {
     for (int q = 0; q < 5; ++q) sc->dev[q] = r[q];
     write_inv_normalisers(sc, cw);
   }
 }
 
-// alpha of the new stage input and counters; after the last stage, t += dt
-__device__ __forceinline__ void fin_alpha_block(const double *pa, const long long *pc, int nblk, Scalars *sc,
-                                                int stage) {
+// alpha of the next stage input, counters, and after the last stage t += dt
+// (stage < 0: outside a step, alpha and counters only)
+__device__ __forceinline__ void finish_alpha_top(const FinBufs &f, int64_t ntiles, Scalars *sc, int stage) {
+  const int64_t ng = num_groups(ntiles);
+  if (!take_ticket(f.tick + 2 * ticket_slots(ntiles) + ng, (unsigned)ng)) return;
   double a[1];
-  fin_reduce<1>(pa, nblk, 0.0, OpMaxNN(), a);
   long long c[2];
-  fin_reduce<2>(pc, nblk, 0LL, OpSum(), c);
+  reduce_top<1>(f.grp_alpha, ng, OpMaxNN(), a);
+  reduce_top<2>(f.grp_cnt, ng, OpSum(), c);
   if (threadIdx.x == 0) {
     sc->alpha = a[0];
     sc->limited += c[0];
@@ -482,6 +575,36 @@ __device__ __forceinline__ void fin_alpha_block(const double *pa, const long lon
       sc->steps += 1;
     }
   }
+}
+
+// Group level.  In the per-solve finalize kernels block g reduces group g
+// directly; in the batch kernel the block that finishes a group's last tile
+// does (after a group ticket), so both produce the same group results.
+__device__ __forceinline__ bool group_ticket(const FinBufs &f, int kind, int64_t tile, int64_t ntiles) {
+  const int64_t g = tile / TILE_GROUP;
+  return take_ticket(f.tick + kind * ticket_slots(ntiles) + g,
+                     (unsigned)min((int64_t)TILE_GROUP, ntiles - g * TILE_GROUP));
+}
+
+// in-kernel finalisation after tile `tile` wrote its partials (batch kernel)
+__device__ __forceinline__ void finish_means(const double *part_sum, const FinBufs &f, int64_t tile, int64_t ntiles,
+                                             Scalars *sc) {
+  if (!group_ticket(f, 0, tile, ntiles)) return;
+  reduce_group<4>(part_sum, tile / TILE_GROUP, ntiles, f.grp_sum, OpSum());
+  finish_means_top(f, ntiles, sc);
+}
+__device__ __forceinline__ void finish_deviations(const double *part_dev, const FinBufs &f, int64_t tile,
+                                                  int64_t ntiles, Scalars *sc, int cw) {
+  if (!group_ticket(f, 1, tile, ntiles)) return;
+  reduce_group<5>(part_dev, tile / TILE_GROUP, ntiles, f.grp_dev, OpMaxNN());
+  finish_deviations_top(f, ntiles, sc, cw);
+}
+__device__ __forceinline__ void finish_alpha(const double *part_alpha, const long long *part_cnt, const FinBufs &f,
+                                             int64_t tile, int64_t ntiles, Scalars *sc, int stage) {
+  if (!group_ticket(f, 2, tile, ntiles)) return;
+  reduce_group<1>(part_alpha, tile / TILE_GROUP, ntiles, f.grp_alpha, OpMaxNN());
+  reduce_group<2>(part_cnt, tile / TILE_GROUP, ntiles, f.grp_cnt, OpSum());
+  finish_alpha_top(f, ntiles, sc, stage);
 }
 
 // dt of the BP CFL condition (Sec. 5), clamped to t_end; inactive once t >= t_end

@@ -31,6 +31,7 @@ struct StageCtx {
   void *tr, *vd, *hs, *ej;
   double *part_sum, *part_dev, *part_alpha;
   long long *part_cnt;
+  FinBufs fin;   // scratch and ticket counters of the in-kernel finalisation
   Scalars *sc;
 };
 
@@ -38,17 +39,17 @@ void launch_geometry(cudaStream_t s, int64_t nt, const double *vxy, const GeomPt
                      double *out_min4);
 void launch_rk(const StageCtx &c, const StateBuf &v, const StateBuf &un, const StateBuf &uh, double a, double b,
                double c_in);
-void launch_fin_mean(const StageCtx &c);
 void launch_rk_only(const StageCtx &c, const StateBuf &v, const StateBuf &un, const StateBuf &uh, double a,
                     double b, double c_in);
+void launch_fin_mean(const StageCtx &c);
+void launch_stats(const StageCtx &c, const StateBuf &uh, double c_out);
 void launch_stats_only(const StageCtx &c, const StateBuf &uh, double c_out);
 void launch_fin_dev(const StageCtx &c);
+void launch_oe_bp(const StageCtx &c, const StateBuf &uh, const StateBuf &out, int do_oe, int do_bp, double c_out,
+                  int stage);
 void launch_oe_bp_only(const StageCtx &c, const StateBuf &uh, const StateBuf &out, int do_oe, int do_bp,
                        double c_out);
 void launch_fin_alpha(const StageCtx &c, int stage);
-void launch_stats(const StageCtx &c, const StateBuf &uh, double c_out);
-void launch_oe_bp(const StageCtx &c, const StateBuf &uh, const StateBuf &out, int do_oe, int do_bp, double c_out,
-                  int stage);
 void launch_step_begin(const StageCtx &c);
 void launch_set_active(const StageCtx &c, int active);
 void launch_set_inv_normalisers(const StageCtx &c);

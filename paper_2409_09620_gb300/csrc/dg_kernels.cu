@@ -111,21 +111,25 @@ __global__ void k_fin_min4(const double *part, int nblk, double *out) {
     for (int q = 0; q < 4; ++q) out[q] = r[q];
 }
 
-__global__ void k_fin_mean(const double *part, int nblk, Scalars *sc) {
+// Finalize kernels: block g reduces tile group g (TILE_GROUP tiles) of the
+// stage kernel's partials; the block that takes the last top-level ticket
+// reduces the group results and writes the scalars (see finish_*_top).
+__global__ void __launch_bounds__(TPB) k_fin_mean(const double *part, FinBufs f, int64_t ntiles, Scalars *sc) {
   if (!sc->active) return;
-  fin_mean_block(part, nblk, sc);
+  reduce_group<4>(part, blockIdx.x, ntiles, f.grp_sum, OpSum());
+  finish_means_top(f, ntiles, sc);
 }
-
-// sup deviations, then the reciprocal normalisers of the OE: a component whose
-// deviation is below 1e-12 max(1, |mean|) counts as constant (delta = 0)
-__global__ void k_fin_dev(const double *part, int nblk, Scalars *sc, int cw) {
+__global__ void __launch_bounds__(TPB) k_fin_dev(const double *part, FinBufs f, int64_t ntiles, Scalars *sc, int cw) {
   if (!sc->active) return;
-  fin_dev_block(part, nblk, sc, cw);
+  reduce_group<5>(part, blockIdx.x, ntiles, f.grp_dev, OpMaxNN());
+  finish_deviations_top(f, ntiles, sc, cw);
 }
-
-__global__ void k_fin_alpha(const double *pa, const long long *pc, int nblk, Scalars *sc, int stage) {
+__global__ void __launch_bounds__(TPB) k_fin_alpha(const double *pa, const long long *pc, FinBufs f, int64_t ntiles,
+                                                   Scalars *sc, int stage) {
   if (!sc->active) return;
-  fin_alpha_block(pa, pc, nblk, sc, stage);
+  reduce_group<1>(pa, blockIdx.x, ntiles, f.grp_alpha, OpMaxNN());
+  reduce_group<2>(pc, blockIdx.x, ntiles, f.grp_cnt, OpSum());
+  finish_alpha_top(f, ntiles, sc, stage);
 }
 
 __global__ void k_step_begin(Scalars *sc) {
@@ -155,23 +159,23 @@ void launch_geometry(cudaStream_t s, int64_t nt, const double *vxy, const GeomPt
 
 template <int K, typename Real>
 static void rk_impl(cudaStream_t s, const MeshDev &m, const Phys &ph, StateDev<Real> v, StateDev<Real> un,
-                    StateDev<Real> uh, const void *tr, void *vd, void *hs, double *part_sum, Scalars *sc, double a,
-                    double b, double c_in) {
+                    StateDev<Real> uh, const void *tr, void *vd, void *hs, double *part_sum, const Scalars *sc,
+                    double a, double b, double c_in) {
   k_rk<K, Real><<<nblocks(m.nt), TPB, 0, s>>>(m, ph, v, un, uh, (const Real *)tr, (Real *)vd, (Real *)hs, part_sum,
                                               sc, a, b, c_in);
 }
 template <int K, typename Real>
 static void stats_impl(cudaStream_t s, const MeshDev &m, const Phys &ph, StateDev<Real> uh, double *part_dev,
-                       const void *vd, const void *hs, void *ej, Scalars *sc, double c_out) {
+                       const void *vd, const void *hs, void *ej, const Scalars *sc, double c_out) {
   k_stats<K, Real><<<nblocks(m.nt), TPB, 0, s>>>(m, ph, uh, part_dev, (const Real *)vd, (const Real *)hs, (Real *)ej,
                                                  sc, c_out);
 }
 template <int K, typename Real>
 static void oebp_impl(cudaStream_t s, const MeshDev &m, const Phys &ph, StateDev<Real> uh, StateDev<Real> out,
-                      const void *ej, void *tr, double *pa, long long *pc, Scalars *sc, int do_oe, int do_bp,
-                      double c_out) {
-  k_oe_bp<K, Real><<<nblocks(m.nt), TPB, 0, s>>>(m, ph, uh, out, (const Real *)ej, (Real *)tr, pa, pc, sc, do_oe, do_bp,
-                                                 c_out);
+                      const void *ej, void *tr, double *pa, long long *pc, const Scalars *sc, int do_oe,
+                      int do_bp, double c_out) {
+  k_oe_bp<K, Real><<<nblocks(m.nt), TPB, 0, s>>>(m, ph, uh, out, (const Real *)ej, (Real *)tr, pa, pc, sc, do_oe,
+                                                 do_bp, c_out);
 }
 
 #define DG_DISPATCH(K_, PREC_, CALL)                        \
@@ -187,11 +191,17 @@ static void oebp_impl(cudaStream_t s, const MeshDev &m, const Phys &ph, StateDev
     }                                                        \
   } while (0)
 
+// k_rk: volume + edge fluxes + RK combination, block sums of |K| u_h^(0)
 void launch_rk_only(const StageCtx &c, const StateBuf &v, const StateBuf &un, const StateBuf &uh, double a,
                     double b, double c_in) {
   DG_DISPATCH(c.k, c.prec,
               (rk_impl<KK, Real>(c.stream, c.mesh, c.phys, {v.avg, (Real *)v.hi}, {un.avg, (Real *)un.hi},
                                  {uh.avg, (Real *)uh.hi}, c.tr, c.vd, c.hs, c.part_sum, c.sc, a, b, c_in)));
+}
+
+void launch_fin_mean(const StageCtx &c) {
+  const int64_t nt = nblocks(c.mesh.nt);
+  k_fin_mean<<<(unsigned)num_groups(nt), TPB, 0, c.stream>>>(c.part_sum, c.fin, nt, c.sc);
 }
 
 void launch_rk(const StageCtx &c, const StateBuf &v, const StateBuf &un, const StateBuf &uh, double a, double b,
@@ -200,10 +210,7 @@ void launch_rk(const StageCtx &c, const StateBuf &v, const StateBuf &un, const S
   launch_fin_mean(c);
 }
 
-void launch_fin_mean(const StageCtx &c) {
-  k_fin_mean<<<1, FIN_THREADS, 0, c.stream>>>(c.part_sum, (int)nblocks(c.mesh.nt), c.sc);
-}
-
+// k_stats: deviation maxima at the volume points and the edge OE records
 void launch_stats_only(const StageCtx &c, const StateBuf &uh, double c_out) {
   DG_DISPATCH(c.k, c.prec,
               (stats_impl<KK, Real>(c.stream, c.mesh, c.phys, {uh.avg, (Real *)uh.hi}, c.part_dev, c.vd, c.hs, c.ej,
@@ -211,7 +218,8 @@ void launch_stats_only(const StageCtx &c, const StateBuf &uh, double c_out) {
 }
 
 void launch_fin_dev(const StageCtx &c) {
-  k_fin_dev<<<1, FIN_THREADS, 0, c.stream>>>(c.part_dev, (int)nblocks(c.mesh.nt), c.sc, c.phys.oe == 2);
+  const int64_t nt = nblocks(c.mesh.nt);
+  k_fin_dev<<<(unsigned)num_groups(nt), TPB, 0, c.stream>>>(c.part_dev, c.fin, nt, c.sc, c.phys.oe == 2);
 }
 
 void launch_stats(const StageCtx &c, const StateBuf &uh, double c_out) {
@@ -219,6 +227,7 @@ void launch_stats(const StageCtx &c, const StateBuf &uh, double c_out) {
   launch_fin_dev(c);
 }
 
+// k_oe_bp: RIOE + limiter + traces, block maxima of the wave speed and counters
 void launch_oe_bp_only(const StageCtx &c, const StateBuf &uh, const StateBuf &out, int do_oe, int do_bp,
                        double c_out) {
   DG_DISPATCH(c.k, c.prec,
@@ -226,8 +235,10 @@ void launch_oe_bp_only(const StageCtx &c, const StateBuf &uh, const StateBuf &ou
                                    c.tr, c.part_alpha, c.part_cnt, c.sc, do_oe, do_bp, c_out)));
 }
 
+// alpha and counters; after stage 2 also t += dt (stage < 0: outside a step)
 void launch_fin_alpha(const StageCtx &c, int stage) {
-  k_fin_alpha<<<1, FIN_THREADS, 0, c.stream>>>(c.part_alpha, c.part_cnt, (int)nblocks(c.mesh.nt), c.sc, stage);
+  const int64_t nt = nblocks(c.mesh.nt);
+  k_fin_alpha<<<(unsigned)num_groups(nt), TPB, 0, c.stream>>>(c.part_alpha, c.part_cnt, c.fin, nt, c.sc, stage);
 }
 
 void launch_oe_bp(const StageCtx &c, const StateBuf &uh, const StateBuf &out, int do_oe, int do_bp, double c_out,

@@ -69,8 +69,8 @@ __device__ __forceinline__ void eval_fixed(const double avg[4], const Real hi[4]
 template <int K, typename Real>
 __device__ __forceinline__ void rk_tile(const MeshDev &m, const Phys &ph, StateDev<Real> v, StateDev<Real> un,
                                         StateDev<Real> uh, const Real *__restrict__ tr, Real *__restrict__ vdo,
-                                        Real *__restrict__ hso, double *__restrict__ part_sum,
-                                        const Scalars *__restrict__ sc, double a, double b, double c_in,
+                                        Real *__restrict__ hso, double *part_sum,
+                                        const Scalars *sc, double a, double b, double c_in,
                                         int64_t tile) {
   constexpr int NB = Deg<K>::NB, NQ = Deg<K>::NQ, NV = Deg<K>::NV;
   const int64_t nt = m.nt;
@@ -255,11 +255,10 @@ __device__ __forceinline__ void rk_tile(const MeshDev &m, const Phys &ph, StateD
 }
 
 template <int K, typename Real>
-__global__ void __launch_bounds__(TPB, sizeof(Real) == 4 ? RK_MINB_F : RK_MINB_D) k_rk(MeshDev m, Phys ph, StateDev<Real> v, StateDev<Real> un,
-                                            StateDev<Real> uh, const Real *__restrict__ tr,
-                                            Real *__restrict__ vdo, Real *__restrict__ hso,
-                                            double *__restrict__ part_sum, const Scalars *__restrict__ sc,
-                                            double a, double b, double c_in) {
+__global__ void __launch_bounds__(TPB, sizeof(Real) == 4 ? RK_MINB_F : RK_MINB_D)
+    k_rk(MeshDev m, Phys ph, StateDev<Real> v, StateDev<Real> un, StateDev<Real> uh, const Real *__restrict__ tr,
+         Real *__restrict__ vdo, Real *__restrict__ hso, double *part_sum, const Scalars *sc, double a, double b,
+         double c_in) {
   if (!sc->active) return;
   rk_tile<K, Real>(m, ph, v, un, uh, tr, vdo, hso, part_sum, sc, a, b, c_in, blockIdx.x);
 }
@@ -268,8 +267,8 @@ __global__ void __launch_bounds__(TPB, sizeof(Real) == 4 ? RK_MINB_F : RK_MINB_D
 // K2: sup deviations from the domain mean at the volume points
 // ==========================================================================
 template <int K, typename Real>
-__device__ __forceinline__ void stats_tile(const MeshDev &m, StateDev<Real> uh, double *__restrict__ part_dev,
-                                           const Scalars *__restrict__ sc, int64_t tile) {
+__device__ __forceinline__ void stats_tile(const MeshDev &m, StateDev<Real> uh, double *part_dev,
+                                           const Scalars *sc, int64_t tile) {
   constexpr int NB = Deg<K>::NB, NV = Deg<K>::NV;
   const int64_t nt = m.nt;
   const int64_t Kc = tile * TPB + threadIdx.x;
@@ -371,7 +370,7 @@ __device__ __forceinline__ void ghost_vertex(int tag, const Real val[4], const R
 template <int K, typename Real>
 __device__ __forceinline__ void edge_tile(const MeshDev &m, const Phys &ph, const Real *__restrict__ vdi,
                                           const Real *__restrict__ hsi, Real *__restrict__ ej,
-                                          const Scalars *__restrict__ sc, double c_out, int64_t tile) {
+                                          const Scalars *sc, double c_out, int64_t tile) {
   const int64_t nt = m.nt;
   const int64_t e0 = m.etile[tile], e1 = m.etile[tile + 1];
   const double t_out = sc->t + c_out * sc->dt;
@@ -738,8 +737,8 @@ __device__ __forceinline__ void limit_and_trace_mixed(const MeshDev &m, const Ph
 template <int K, typename Real>
 __device__ __forceinline__ void oe_bp_tile(const MeshDev &m, const Phys &ph, StateDev<Real> uh, StateDev<Real> out,
                                            const Real *__restrict__ ej,
-                                           Real *__restrict__ tr, double *__restrict__ part_alpha,
-                                           long long *__restrict__ part_cnt, const Scalars *__restrict__ sc,
+                                           Real *__restrict__ tr, double *part_alpha,
+                                           long long *part_cnt, const Scalars *sc,
                                            int do_oe, int do_bp, double c_out, int64_t tile) {
   constexpr int NB = Deg<K>::NB, NQ = Deg<K>::NQ;
   constexpr int NE = 3 * NQ;          // edge Gauss points
@@ -948,21 +947,20 @@ __device__ __forceinline__ void oe_bp_tile(const MeshDev &m, const Phys &ph, Sta
 
 // OE statistics of the tile's cells and the jump data of the edges it owns
 template <int K, typename Real>
-__global__ void __launch_bounds__(TPB, sizeof(Real) == 4 ? STATS_MINB_F : STATS_MINB_D) k_stats(MeshDev m, Phys ph, StateDev<Real> uh, double *__restrict__ part_dev,
-                                               const Real *__restrict__ vdi, const Real *__restrict__ hsi,
-                                               Real *__restrict__ ej, const Scalars *__restrict__ sc, double c_out) {
+__global__ void __launch_bounds__(TPB, sizeof(Real) == 4 ? STATS_MINB_F : STATS_MINB_D)
+    k_stats(MeshDev m, Phys ph, StateDev<Real> uh, double *part_dev, const Real *__restrict__ vdi,
+            const Real *__restrict__ hsi, Real *__restrict__ ej, const Scalars *sc, double c_out) {
   if (!sc->active) return;
   stats_tile<K, Real>(m, uh, part_dev, sc, blockIdx.x);
   edge_tile<K, Real>(m, ph, vdi, hsi, ej, sc, c_out, blockIdx.x);
 }
 
-// the FP32 form is latency-bound: ask for three resident blocks per SM
+// RIOE damping, BP limiter, traces and wave speeds of the stage result
 template <int K, typename Real>
-__global__ void __launch_bounds__(TPB, sizeof(Real) == 4 ? OEBP_MINB_F : OEBP_MINB_D) k_oe_bp(MeshDev m, Phys ph, StateDev<Real> uh,
-                                                                        StateDev<Real> out,
-                                               const Real *__restrict__ ej, Real *__restrict__ tr,
-                                               double *__restrict__ part_alpha, long long *__restrict__ part_cnt,
-                                               const Scalars *__restrict__ sc, int do_oe, int do_bp, double c_out) {
+__global__ void __launch_bounds__(TPB, sizeof(Real) == 4 ? OEBP_MINB_F : OEBP_MINB_D)
+    k_oe_bp(MeshDev m, Phys ph, StateDev<Real> uh, StateDev<Real> out, const Real *__restrict__ ej,
+            Real *__restrict__ tr, double *part_alpha, long long *part_cnt, const Scalars *sc, int do_oe,
+            int do_bp, double c_out) {
   if (!sc->active) return;
   oe_bp_tile<K, Real>(m, ph, uh, out, ej, tr, part_alpha, part_cnt, sc, do_oe, do_bp, c_out, blockIdx.x);
 }

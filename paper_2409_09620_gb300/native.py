@@ -267,8 +267,8 @@ class Solver:
 
     def profile_steps(self, n):
         """n instrumented steps; per kernel kind: (summed ms, launches)."""
-        ms = np.zeros(7)
-        nl = np.zeros(7, np.int64)
+        ms = np.zeros(len(self.KERNEL_KINDS))
+        nl = np.zeros(len(self.KERNEL_KINDS), np.int64)
         _check(lib().dg_profile_steps(self.h, n, _p(ms), _p(nl)))
         return {k: (float(ms[i]), int(nl[i])) for i, k in enumerate(self.KERNEL_KINDS)}
 

@@ -297,3 +297,25 @@ def test_bp_time_step_ratio(oracle_mod, N, k, lo, hi):
     r = a["dt_last"] / b["dt_last"]
     assert lo - 1e-9 <= r <= hi + 1e-9
     np.testing.assert_allclose(r, mesh.min_cfl_area(k, 0) / mesh.min_cfl_area(k, 1), rtol=1e-12)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_profiled_steps_match_graph(oracle_mod, N, precision):
+    """dg_profile_steps launches the kernels of a step one by one with events
+    around them; the state it leaves is bitwise the state of the same number
+    of captured steps, and every kernel kind launches as often as a step has
+    it.  20,000 cells make 157 tiles, so the finalize kernels run with two
+    tile groups, one of them partial; equality after several steps also shows
+    that every ticket counter is back at zero after each launch."""
+    wl = W.sedov_workload(n=100, k=2)
+    _, _, _, s1 = _setup(oracle_mod, N, wl, precision=precision)
+    prof = s1.profile_steps(3)
+    assert {k: v[1] for k, v in prof.items()} == {"step_begin": 3, "rk": 9, "fin_mean": 9, "stats": 9,
+                                                  "fin_dev": 9, "oe_bp": 9, "fin_alpha": 9}
+    assert all(v[0] > 0 for v in prof.values())
+    _, _, _, s2 = _setup(oracle_mod, N, wl, precision=precision)
+    s2.advance(1e30, max_steps=3)
+    u1, t1 = s1.get_state()
+    u2, t2 = s2.get_state()
+    assert t1 == t2 and t1 > 0
+    assert np.array_equal(u1, u2)
