@@ -491,7 +491,7 @@ extern "C" int32_t dg_init(const dg_mesh *mesh, const dg_config *cfg, const doub
   STRY(alloc_state(s, &s->un));
   STRY(alloc_state(s, &s->uh));
   STRY(alloc_state(s, &s->us));
-  STRY(cudaMalloc(&s->tr, rs * nt * 3 * nq * 8));
+  STRY(cudaMalloc(&s->tr, rs * nt * 3 * nq * trace_stride(cfg->precision)));
   STRY(cudaMalloc(&s->vd, rs * nt * VD_CELL));
   STRY(cudaMalloc(&s->hs, rs * nt * 12));
   STRY(cudaMalloc(&s->ej, rs * std::max<int64_t>(mesh->ne, 1) * EJ_STRIDE));

@@ -478,7 +478,7 @@ extern "C" int32_t dg_batch_autotune(dg_batch *b, int32_t steps, int32_t *best_c
     StateBuf un, uh, us;
     solver_states(s, &un, &uh, &us);
     Snap &q = snaps[i];
-    q = Snap{nullptr, nullptr, nullptr, sizeof(double) * 4 * nt, rs * 4 * (nb - 1) * nt, rs * nt * 3 * nq * 8, {}};
+    q = Snap{nullptr, nullptr, nullptr, sizeof(double) * 4 * nt, rs * 4 * (nb - 1) * nt, rs * nt * 3 * nq * trace_stride(core.prec), {}};
     if (cudaMalloc(&q.avg, q.navg) != cudaSuccess || cudaMalloc(&q.hi, q.nhi) != cudaSuccess ||
         cudaMalloc(&q.tr, q.ntr) != cudaSuccess) {
       free_snaps();

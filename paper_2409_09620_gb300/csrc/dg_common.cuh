@@ -62,6 +62,13 @@ template <> struct Geo<float> {
   static __device__ __forceinline__ const float *hgeo(const MeshDev &m) { return m.hgeo_f; }
 };
 
+// values per edge Gauss point in the trace buffer tr[nt][3][Q][TS]: u and
+// F(u).n in the FP64 form (TS = 8); u only in the FP32 form (TS = 4), whose
+// stage kernel recomputes F(u).n in FP32 on both sides of the edge.  The two
+// cells of an edge have exactly opposite normals, so the recomputed fluxes
+// are the negated values the other cell uses, bit for bit.
+template <typename Real> struct TraceStride { static constexpr int value = sizeof(Real) == 4 ? 4 : 8; };
+__host__ __device__ constexpr int trace_stride(int precision) { return precision == 0 ? 8 : 4; }
 // per-edge OE record ej[ne][EJ_STRIDE]: beta, then sqrt of the trapezoidal
 // jump sums for q = rho, (m_n|m_t max | m1), (m2), E and j = 0..k (13 used)
 constexpr int EJ_STRIDE = 16;

@@ -122,17 +122,30 @@ __device__ __forceinline__ void rk_tile(const MeshDev &m, const Phys &ph, StateD
       const Real li = Geo<Real>::len(m)[i * nt + Kc];
 #pragma unroll
       for (int nu = 0; nu < NQ; ++nu) {
-        Real ow[8], um[4], fm[4], up[4], fp[4];
-        vload<8>(tr + ((Kc * 3 + i) * NQ + nu) * 8, ow);
+        constexpr int TS = TraceStride<Real>::value;
+        Real ow[TS], um[4], fm[4], up[4], fp[4];
+        vload<TS>(tr + ((Kc * 3 + i) * NQ + nu) * TS, ow);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) { um[q] = ow[q]; fm[q] = ow[4 + q]; }
+        for (int q = 0; q < 4; ++q) um[q] = ow[q];
+        if constexpr (TS == 8) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) fm[q] = ow[4 + q];
+        } else {
+          flux_dir(um, nx, ny, gm1, fm);
+        }
         if (cn >= 0) {
           const int64_t nb = cn >> 2;
           const int j = cn & 3;
-          Real ot[8];
-          vload<8>(tr + ((nb * 3 + j) * NQ + (NQ - 1 - nu)) * 8, ot);
+          Real ot[TS];
+          vload<TS>(tr + ((nb * 3 + j) * NQ + (NQ - 1 - nu)) * TS, ot);
 #pragma unroll
-          for (int q = 0; q < 4; ++q) { up[q] = ot[q]; fp[q] = -ot[4 + q]; }
+          for (int q = 0; q < 4; ++q) up[q] = ot[q];
+          if constexpr (TS == 8) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) fp[q] = -ot[4 + q];
+          } else {
+            flux_dir(up, nx, ny, gm1, fp);   // = -F(u+).n of the neighbour, n+ = -n exactly
+          }
         } else {
           double px = 0.0, py = 0.0;
           if (cn == -7) {
@@ -479,110 +492,29 @@ __device__ __forceinline__ void edge_tile(const MeshDev &m, const Phys &ph, cons
   }
 }
 
-// --------------------------------------------------------------------------
-// BP limiter and traces of the mixed-precision form (FP32 modes, FP64 cell
-// averages).  Every point of the limiter set is first screened in FP32 with a
-// margin far above the FP32 evaluation error; a cell that passes is admissible
-// with theta = 1.  Other cells get the paper's theta (Sec. 4.4) in FP64, with
-// the targets raised by the rounding that storing the scaled modes in FP32
-// can cause; the stored state is then re-evaluated in FP64 at every point and,
-// if a bound still fails, the cell falls back to its (admissible) average.
-// --------------------------------------------------------------------------
+// The FP64 branch of limit_and_trace_mixed for cells that fail the FP32
+// screen (rare: cells where the limiter acts).  Kept out of line so that its
+// registers do not weigh on the common path.  hi, a0: the cell's modes and
+// averages; px, py: the extra limiter points; ut: traces of the stored state
+// at the edge Gauss points (out); limited: set when theta < 1 or the cell
+// fell back to its average.
 template <int K>
-__device__ __forceinline__ void limit_and_trace_mixed(const MeshDev &m, const Phys &ph, const double a0[4],
-                                                      float hi[4][Deg<K>::NB], const float nxs[3],
-                                                      const float nys[3], const int32_t cns[3], StateDev<float> out,
-                                                      float *tr, int64_t Kc, double t_out, int do_bp, double &amax,
-                                                      long long cnt[2]) {
+__device__ __noinline__ void limit_mixed_fp64(const MeshDev &m, const Phys &ph, const double *a0p, const float *hip,
+                                              const double *pxp, const double *pyp, StateDev<float> out, int64_t Kc,
+                                              float *utp, long long *limited) {
   constexpr int NB = Deg<K>::NB, NQ = Deg<K>::NQ, NE = 3 * NQ;
   const int64_t nt = m.nt;
-  const float gamma = float(ph.gamma), gm1 = float(ph.gamma - 1.0);
-  // the two extra points of the limiter set (P1: vertices v1, v2; P2: internal nodes)
-  double px[2], py[2];
-  if (K == 1) {
-    const int v1 = m.limv[Kc], v2 = m.limv[nt + Kc];
-    px[0] = vert_xi(v1); py[0] = vert_eta(v1); px[1] = vert_xi(v2); py[1] = vert_eta(v2);
-  } else {
-    px[0] = m.node[Kc]; py[0] = m.node[nt + Kc]; px[1] = m.node[2 * nt + Kc]; py[1] = m.node[3 * nt + Kc];
+  double a0[4], px[2], py[2];
+  float hi[4][NB];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    a0[c] = a0p[c];
+#pragma unroll
+    for (int l = 0; l < NB; ++l) hi[c][l] = hip[c * NB + l];
   }
-  // FP32 deviations u - ubar at the edge Gauss points
-  float df[NE][4];
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int nu = 0; nu < NQ; ++nu) {
-      const double xi = edge_xi(i, gauss_s(NQ, nu)), eta = edge_eta(i, gauss_s(NQ, nu));
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        float sacc = 0.0f;
-#pragma unroll
-        for (int l = 1; l < NB; ++l) sacc = cfma(psi(l, xi, eta), hi[c][l], sacc);
-        df[i * NQ + nu][c] = sacc;
-      }
-    }
-  bool lim64 = false;
-  if (do_bp) {
-    const double Ebar = int_energy(a0);
-    if (!(a0[0] > 0.0) || !(Ebar > 0.0)) {
-      cnt[1] = 1;
-    } else {
-      float S[4];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        S[c] = fabsf(float(a0[c]));
-#pragma unroll
-        for (int l = 1; l < NB; ++l) S[c] += 4.0f * fabsf(hi[c][l]);   // |Psi_l| <= 4 on K
-      }
-      const float eps1 = float(fmin(a0[0], 1e-13)), eps2 = float(fmin(Ebar, 1e-13));
-      auto passes = [&](const float d[4]) -> bool {
-        const float r = float(a0[0]) + d[0];
-        if (!(r >= eps1 + 1e-5f * S[0])) return false;
-        const float m1 = float(a0[1]) + d[1], m2 = float(a0[2]) + d[2], E = float(a0[3]) + d[3];
-        const float ri = 1.0f / r;
-        const float q = (m1 * m1 + m2 * m2) * ri;           // |m|^2 / rho
-        const float v = sqrtf(q * ri);                       // |v|
-        const float margin = 1e-5f * (S[3] + v * (S[1] + S[2]) + v * v * S[0]) + 1e-6f * (fabsf(E) + q);
-        return E - 0.5f * q >= eps2 + margin;
-      };
-      bool ok = true;
-#pragma unroll
-      for (int p = 0; p < NE; ++p) ok = passes(df[p]) && ok;
-      float dx[NE + 2][4];
-      if (ph.decomp) {
-#pragma unroll
-        for (int p = 0; p < NE; ++p)
-#pragma unroll
-          for (int c = 0; c < 4; ++c) dx[p][c] = df[p][c];
-        zxs_extra_points<K, float, NE + 2>(dx);
-      } else {
-#pragma unroll
-        for (int p = 0; p < 2; ++p)
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            float sacc = 0.0f;
-#pragma unroll
-            for (int l = 1; l < NB; ++l) sacc = fmaf(float(psi(l, px[p], py[p])), hi[c][l], sacc);
-            dx[NE + p][c] = sacc;
-          }
-      }
-#pragma unroll
-      for (int p = 0; p < 2; ++p) ok = passes(dx[NE + p]) && ok;
-      lim64 = !ok;
-    }
-  }
+  px[0] = pxp[0]; px[1] = pxp[1]; py[0] = pyp[0]; py[1] = pyp[1];
   float ut[NE][4];
-  if (!lim64) {
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      out.avg[c * nt + Kc] = a0[c];
-#pragma unroll
-      for (int l = 1; l < NB; ++l) out.hi[(c * (NB - 1) + (l - 1)) * nt + Kc] = hi[c][l];
-    }
-#pragma unroll
-    for (int p = 0; p < NE; ++p)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) ut[p][c] = float(a0[c]) + df[p][c];
-  } else {
+  long long cnt[1] = {0};
     // ---- FP64 theta (Sec. 4.4 Steps 1-2) with targets covering the FP32 store
     double d[NE + 2][4], Sa[4];
 #pragma unroll
@@ -700,6 +632,133 @@ __device__ __forceinline__ void limit_and_trace_mixed(const MeshDev &m, const Ph
     for (int p = 0; p < NE; ++p)
 #pragma unroll
       for (int c = 0; c < 4; ++c) ut[p][c] = float(ud[p][c]);
+  #pragma unroll
+  for (int p = 0; p < NE; ++p)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) utp[p * 4 + c] = ut[p][c];
+  *limited = cnt[0];
+}
+
+// --------------------------------------------------------------------------
+// BP limiter and traces of the mixed-precision form (FP32 modes, FP64 cell
+// averages).  Every point of the limiter set is first screened in FP32 with a
+// margin far above the FP32 evaluation error; a cell that passes is admissible
+// with theta = 1.  Other cells get the paper's theta (Sec. 4.4) in FP64, with
+// the targets raised by the rounding that storing the scaled modes in FP32
+// can cause; the stored state is then re-evaluated in FP64 at every point and,
+// if a bound still fails, the cell falls back to its (admissible) average.
+// --------------------------------------------------------------------------
+template <int K>
+__device__ __forceinline__ void limit_and_trace_mixed(const MeshDev &m, const Phys &ph, const double a0[4],
+                                                      float hi[4][Deg<K>::NB], const float nxs[3],
+                                                      const float nys[3], const int32_t cns[3], StateDev<float> out,
+                                                      float *tr, int64_t Kc, double t_out, int do_bp, double &amax,
+                                                      long long cnt[2]) {
+  constexpr int NB = Deg<K>::NB, NQ = Deg<K>::NQ, NE = 3 * NQ;
+  const int64_t nt = m.nt;
+  const float gamma = float(ph.gamma), gm1 = float(ph.gamma - 1.0);
+  // the two extra points of the limiter set (P1: vertices v1, v2; P2: internal nodes)
+  double px[2], py[2];
+  if (K == 1) {
+    const int v1 = m.limv[Kc], v2 = m.limv[nt + Kc];
+    px[0] = vert_xi(v1); py[0] = vert_eta(v1); px[1] = vert_xi(v2); py[1] = vert_eta(v2);
+  } else {
+    px[0] = m.node[Kc]; py[0] = m.node[nt + Kc]; px[1] = m.node[2 * nt + Kc]; py[1] = m.node[3 * nt + Kc];
+  }
+  // FP32 deviations u - ubar at the edge Gauss points
+  float df[NE][4];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int nu = 0; nu < NQ; ++nu) {
+      const double xi = edge_xi(i, gauss_s(NQ, nu)), eta = edge_eta(i, gauss_s(NQ, nu));
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        float sacc = 0.0f;
+#pragma unroll
+        for (int l = 1; l < NB; ++l) sacc = cfma(psi(l, xi, eta), hi[c][l], sacc);
+        df[i * NQ + nu][c] = sacc;
+      }
+    }
+  bool lim64 = false;
+  if (do_bp) {
+    const double Ebar = int_energy(a0);
+    if (!(a0[0] > 0.0) || !(Ebar > 0.0)) {
+      cnt[1] = 1;
+    } else {
+      float S[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        S[c] = fabsf(float(a0[c]));
+#pragma unroll
+        for (int l = 1; l < NB; ++l) S[c] += 4.0f * fabsf(hi[c][l]);   // |Psi_l| <= 4 on K
+      }
+      const float eps1 = float(fmin(a0[0], 1e-13)), eps2 = float(fmin(Ebar, 1e-13));
+      auto passes = [&](const float d[4]) -> bool {
+        const float r = float(a0[0]) + d[0];
+        if (!(r >= eps1 + 1e-5f * S[0])) return false;
+        const float m1 = float(a0[1]) + d[1], m2 = float(a0[2]) + d[2], E = float(a0[3]) + d[3];
+        const float ri = 1.0f / r;
+        const float q = (m1 * m1 + m2 * m2) * ri;           // |m|^2 / rho
+        const float v = sqrtf(q * ri);                       // |v|
+        const float margin = 1e-5f * (S[3] + v * (S[1] + S[2]) + v * v * S[0]) + 1e-6f * (fabsf(E) + q);
+        return E - 0.5f * q >= eps2 + margin;
+      };
+      bool ok = true;
+#pragma unroll
+      for (int p = 0; p < NE; ++p) ok = passes(df[p]) && ok;
+      float dx[NE + 2][4];
+      if (ph.decomp) {
+#pragma unroll
+        for (int p = 0; p < NE; ++p)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) dx[p][c] = df[p][c];
+        zxs_extra_points<K, float, NE + 2>(dx);
+      } else {
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            float sacc = 0.0f;
+#pragma unroll
+            for (int l = 1; l < NB; ++l) sacc = fmaf(float(psi(l, px[p], py[p])), hi[c][l], sacc);
+            dx[NE + p][c] = sacc;
+          }
+      }
+#pragma unroll
+      for (int p = 0; p < 2; ++p) ok = passes(dx[NE + p]) && ok;
+      lim64 = !ok;
+    }
+  }
+  float ut[NE][4];
+  if (!lim64) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      out.avg[c * nt + Kc] = a0[c];
+#pragma unroll
+      for (int l = 1; l < NB; ++l) out.hi[(c * (NB - 1) + (l - 1)) * nt + Kc] = hi[c][l];
+    }
+#pragma unroll
+    for (int p = 0; p < NE; ++p)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) ut[p][c] = float(a0[c]) + df[p][c];
+  } else {
+    // FP64 theta (Sec. 4.4 Steps 1-2) out of line
+    double a0l[4], pxl[2] = {px[0], px[1]}, pyl[2] = {py[0], py[1]};
+    float hl[4][NB], utl[NE][4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      a0l[c] = a0[c];
+#pragma unroll
+      for (int l = 0; l < NB; ++l) hl[c][l] = hi[c][l];
+    }
+    long long lim = 0;
+    limit_mixed_fp64<K>(m, ph, a0l, &hl[0][0], pxl, pyl, out, Kc, &utl[0][0], &lim);
+    if (lim) cnt[0] = 1;
+#pragma unroll
+    for (int p = 0; p < NE; ++p)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) ut[p][c] = utl[p][c];
   }
   // traces, F.n and wave speed at the edge Gauss points for the next stage
   float amax32 = 0.0f;
@@ -711,10 +770,7 @@ __device__ __forceinline__ void limit_and_trace_mixed(const MeshDev &m, const Ph
       const float *u = ut[i * NQ + nu];
       const float r = flux_speed(u, nxs[i], nys[i], gm1, gamma, f);
       amax32 = (r > amax32 || r != r) ? r : amax32;
-      float o8[8];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) { o8[q] = u[q]; o8[4 + q] = f[q]; }
-      vstore<8>(tr + ((Kc * 3 + i) * NQ + nu) * 8, o8);
+      vstore<4>(tr + ((Kc * 3 + i) * NQ + nu) * 4, u);   // u only: k_rk recomputes F(u).n
       if (cns[i] <= -3) {
         double qx = 0.0, qy = 0.0;
         if (cns[i] == -7) {
