@@ -50,8 +50,8 @@ __device__ __forceinline__ void load_state(const StateDev<Real> &s, int64_t nt, 
 }
 
 // value of the cell polynomial at a fixed reference point (compile-time after unrolling)
-template <typename Real, int NB>
-__device__ __forceinline__ void eval_fixed(const double avg[4], const Real hi[4][NB], double xi, double eta,
+template <typename Real, int NB, typename A>
+__device__ __forceinline__ void eval_fixed(const A avg[4], const Real hi[4][NB], double xi, double eta,
                                            Real out[4]) {
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
@@ -61,6 +61,17 @@ __device__ __forceinline__ void eval_fixed(const double avg[4], const Real hi[4]
     out[c] = s;
   }
 }
+
+// In the FP32 form the FP64 averages are converted once and then let go, so
+// that the compiler cannot re-convert them at every use (each conversion is
+// an FP64-pipe instruction); the FP64 value is reloaded where it is needed
+// again.  In the FP64 form these are plain copies.
+template <typename Real>
+__device__ __forceinline__ void to_real(const double a[4], Real r[4]) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) r[c] = Real(a[c]);
+}
+__device__ __forceinline__ double reload_avg(const double *p) { return __ldcg(p); }
 
 // ==========================================================================
 // K1: u_h = a u_n + b (v + dt L(v))
@@ -85,6 +96,8 @@ __device__ __forceinline__ void rk_tile(const MeshDev &m, const Phys &ph, StateD
     double v0[4];
     Real cv[4][NB];
     load_state<Real, NB>(v, nt, Kc, v0, cv);
+    Real v0r[4];
+    to_real(v0, v0r);
 
     // ---- volume term: |K| sum_mu w_mu F(u(x_mu)) . grad Psi_l ---------------
     Real acc[4][NB];
@@ -96,7 +109,7 @@ __device__ __forceinline__ void rk_tile(const MeshDev &m, const Phys &ph, StateD
     for (int mu = 0; mu < NV; ++mu) {
       const double xi = vol_xi(NV, mu), eta = vol_eta(NV, mu), w = vol_w(NV, mu);
       Real u[4], g1[4], g2[4];
-      eval_fixed<Real, NB>(v0, cv, xi, eta, u);
+      eval_fixed<Real, NB>(v0r, cv, xi, eta, u);
       // F . grad Psi = (F . grad xi) dPsi/dxi + (F . grad eta) dPsi/deta
       flux_dir2(u, jx, jy, ex, ey, gm1, g1, g2);
 #pragma unroll
@@ -197,11 +210,14 @@ __device__ __forceinline__ void rk_tile(const MeshDev &m, const Phys &ph, StateD
     const double dta = dt * m.iarea[Kc];
     double h0[4];
     Real hh[4][NB];
+    Real h0r[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      h0[c] = a * un0[c] + b * (v0[c] + dta * acc0[c]);
+      const double v0c = sizeof(Real) == sizeof(double) ? v0[c] : reload_avg(v.avg + c * nt + Kc);
+      h0[c] = a * un0[c] + b * (v0c + dta * acc0[c]);
       uh.avg[c * nt + Kc] = h0[c];
       mass[c] = area * h0[c];
+      h0r[c] = Real(h0[c]);
       hh[c][0] = Real(0);
 #pragma unroll
       for (int l = 1; l < NB; ++l) {
@@ -221,7 +237,7 @@ __device__ __forceinline__ void rk_tile(const MeshDev &m, const Phys &ph, StateD
       Real val4[4];
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        Real val = Real(h0[c]), gx = Real(0), ge = Real(0);
+        Real val = h0r[c], gx = Real(0), ge = Real(0);
 #pragma unroll
         for (int l = 1; l < NB; ++l) {
           val = cfma(psi(l, xi, eta), hh[c][l], val);
@@ -680,24 +696,32 @@ __device__ __forceinline__ void limit_and_trace_mixed(const MeshDev &m, const Ph
         df[i * NQ + nu][c] = sacc;
       }
     }
+  // the averages are unchanged by the limiter: store them now, take what is
+  // needed in FP64, and continue with FP32 copies (the rare FP64 branch
+  // reloads them)
+#pragma unroll
+  for (int c = 0; c < 4; ++c) out.avg[c * nt + Kc] = a0[c];
+  const double Ebar = int_energy(a0);
+  const bool avg_ok = (a0[0] > 0.0) && (Ebar > 0.0);
+  const float eps1 = float(fmin(a0[0], 1e-13)), eps2 = float(fmin(Ebar, 1e-13));
+  float a0f[4];
+  to_real(a0, a0f);
   bool lim64 = false;
   if (do_bp) {
-    const double Ebar = int_energy(a0);
-    if (!(a0[0] > 0.0) || !(Ebar > 0.0)) {
+    if (!avg_ok) {
       cnt[1] = 1;
     } else {
       float S[4];
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        S[c] = fabsf(float(a0[c]));
+        S[c] = fabsf(a0f[c]);
 #pragma unroll
         for (int l = 1; l < NB; ++l) S[c] += 4.0f * fabsf(hi[c][l]);   // |Psi_l| <= 4 on K
       }
-      const float eps1 = float(fmin(a0[0], 1e-13)), eps2 = float(fmin(Ebar, 1e-13));
       auto passes = [&](const float d[4]) -> bool {
-        const float r = float(a0[0]) + d[0];
+        const float r = a0f[0] + d[0];
         if (!(r >= eps1 + 1e-5f * S[0])) return false;
-        const float m1 = float(a0[1]) + d[1], m2 = float(a0[2]) + d[2], E = float(a0[3]) + d[3];
+        const float m1 = a0f[1] + d[1], m2 = a0f[2] + d[2], E = a0f[3] + d[3];
         const float ri = 1.0f / r;
         const float q = (m1 * m1 + m2 * m2) * ri;           // |m|^2 / rho
         const float v = sqrtf(q * ri);                       // |v|
@@ -733,22 +757,20 @@ __device__ __forceinline__ void limit_and_trace_mixed(const MeshDev &m, const Ph
   float ut[NE][4];
   if (!lim64) {
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      out.avg[c * nt + Kc] = a0[c];
+    for (int c = 0; c < 4; ++c)
 #pragma unroll
       for (int l = 1; l < NB; ++l) out.hi[(c * (NB - 1) + (l - 1)) * nt + Kc] = hi[c][l];
-    }
 #pragma unroll
     for (int p = 0; p < NE; ++p)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) ut[p][c] = float(a0[c]) + df[p][c];
+      for (int c = 0; c < 4; ++c) ut[p][c] = a0f[c] + df[p][c];
   } else {
     // FP64 theta (Sec. 4.4 Steps 1-2) out of line
     double a0l[4], pxl[2] = {px[0], px[1]}, pyl[2] = {py[0], py[1]};
     float hl[4][NB], utl[NE][4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      a0l[c] = a0[c];
+      a0l[c] = reload_avg(out.avg + c * nt + Kc);
 #pragma unroll
       for (int l = 0; l < NB; ++l) hl[c][l] = hi[c][l];
     }
