@@ -38,18 +38,22 @@ METRIC = "P2 Euler DG cell-stage updates/s (FP64 vs FP32), HBM GB/s; p50/p99 sol
 UNIT = "cell-stage updates/s"
 
 # Algorithmic FP64 work per cell-stage of each kernel kind (P2 interior cell),
-# counted from the kernel source in the conventional way: add / sub / mul = 1
-# flop, fma = 2, and one flop for each division, square root and exponential.
-# "stats" is the launch that computes the volume-point deviations (270 per
-# cell) and the per-edge OE records (about 277 per edge, 1.5 edges per cell).
-ALGO_FLOPS_P2 = {"rk": 2110.0, "stats": 685.0, "oe_bp": 1615.0}
-# FP64 flops per cell-stage that the hardware executed for the same kernels
-# (2 DFMA + DADD + DMUL per launch from one ncu capture / cells); division,
-# square root and exp expand into DFMA sequences.  None = not re-measured since
-# the kernel last changed.
-EXECUTED_FLOPS_P2 = {"rk": None, "oe_bp": None, "stats": None}
-# DRAM bytes per launch of the dominant kernel from the same ncu capture.
-TRAFFIC_PER_LAUNCH = {"rk": None, "oe_bp": None, "stats": None}
+# counted from the kernel source: add / sub / mul = 1 flop, fma = 2, one flop
+# for each division, square root and exponential, coefficients that are zero
+# at the fixed quadrature points skipped.  k_rk: volume evaluation 208, volume
+# fluxes 186, volume accumulation 240, edge terms 565, mass inverse and RK
+# combination 150, vertex records 361, Hessians 156, block sums 6.  k_stats:
+# deviations at the volume points 236, edge OE records 277 per edge x 1.5.
+# k_oe_bp: sigma 141, damping 38, limiter at the 11 points 595, traces and
+# wave speeds 288.
+ALGO_FLOPS_P2 = {"rk": 1872.0, "stats": 652.0, "oe_bp": 1062.0}
+# FP64 flops per cell-stage the hardware executed for the same kernels
+# (2 DFMA + DMUL + DADD from one ncu capture / cells); division, square root
+# and exp expand into DFMA sequences.  None = not re-measured since the kernel
+# last changed.
+EXECUTED_FLOPS_P2 = {"rk": 2089.0, "stats": 913.0, "oe_bp": 1435.0}
+# DRAM bytes (read + write) per launch from the same ncu capture.
+TRAFFIC_PER_LAUNCH = {"rk": 1.638e9, "stats": 0.951e9, "oe_bp": 1.320e9}
 
 
 def load_peaks():
@@ -230,6 +234,8 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=10)
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-cfl-gain", action="store_true")
+    ap.add_argument("--no-paper-meshes", action="store_true",
+                    help="skip the forward-facing-step and wedge meshes")
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-rate", type=float, default=30.0)
     args = ap.parse_args()
@@ -442,6 +448,56 @@ def main():
                                  "min_cfl_area_ratio": m_g.min_cfl_area(k, 0) / m_g.min_cfl_area(k, 1)}
         cfl_gain["paper_dmr_mean_dt_ratio"] = {"P1": 2.869570, "P2": 4.486689}
 
+    # the paper's own domains (Sec. 5) on near-equilateral lattice meshes of
+    # about its cell counts: throughput, and the mean BP time step of the
+    # optimal over the classical decomposition over the first steps
+    paper_meshes = None
+    if not args.no_paper_meshes:
+        from paper_2409_09620_gb300 import workloads as W
+
+        def ms_per_step(m, w, u, precision, n):
+            sv = N.Solver(m, N.config_for(w, precision=precision), u)
+            stream = torch.cuda.ExternalStream(sv.stream)
+            sv.advance_async(3)
+            sv.sync()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sv.advance_async(n)
+            e1.record(stream)
+            sv.sync()
+            return e0.elapsed_time(e1) / n
+
+        paper_meshes = {}
+        for key, make, paper in (
+                ("ffs", lambda k: W.ffs_workload(k=k),
+                 {"cells": 73862, "mean_dt_ratio": {"P1": 2.851852, "P2": 4.489796}}),
+                ("wedge_dmr", lambda k: W.wedge_dmr_workload(k=k),
+                 {"cells": 828840, "mean_dt_ratio": {"P1": 2.869570, "P2": 4.486689}})):
+            ent = {"paper": paper}
+            for k in (1, 2):
+                w = make(k)
+                m = N.Mesh.from_mesh(w.mesh)
+                u = N.initial_state(m, w)
+                ent["cells"] = w.mesh.nt
+                if k == 2:
+                    for pname, prec in (("fp64", N.PREC_FP64), ("mixed", N.PREC_MIXED)):
+                        ms_k = ms_per_step(m, w, u, prec, 20)
+                        ent[f"P2_{pname}"] = {"ms_per_step": ms_k, "value": w.mesh.nt * 3 / (ms_k / 1e3),
+                                              "unit": UNIT}
+                # 30 steps of the optimal decomposition set the end time; the
+                # classical one runs to the same time
+                s_opt = N.Solver(m, N.config_for(w, decomp=0), u)
+                a_st, _ = s_opt.advance(10.0, max_steps=30)
+                T = a_st["t"]
+                s_zxs = N.Solver(m, N.config_for(w, decomp=1), u)
+                b_st, _ = s_zxs.advance(T)
+                ent[f"P{k}_dt"] = {"T": T, "optimal_steps": a_st["steps"], "classical_steps": b_st["steps"],
+                                   "mean_dt_ratio": b_st["steps"] / a_st["steps"],
+                                   "min_cfl_area_ratio": m.min_cfl_area(k, 0) / m.min_cfl_area(k, 1)}
+                del s_opt, s_zxs
+            paper_meshes[key] = ent
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         wl_full = make_workload(args.workload, args.nx, args.ny)
@@ -460,7 +516,7 @@ def main():
                            "l2": "working set ~1.7 GB > 129 MB L2, no flush"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": 19 * args.steps, "clocks": clocks, "fp32": mixed, "batch": batch,
-                "serving": serving, "bp_cfl_gain": cfl_gain,
+                "serving": serving, "bp_cfl_gain": cfl_gain, "paper_meshes": paper_meshes,
                 "peaks": {"source": peak_src, "hbm_gbs": peaks.get("hbm_gbs")},
                 "stats": {"limited_cells": st["limited_cells"], "cfl_breaches": st["cfl_breaches"],
                           "t": st["t"], "dt_last": st["dt_last"]}}

@@ -11,7 +11,10 @@ both the CUDA path and the CPU oracle consume:
   vertex ``i``, as in the paper's Fig. 1);
 * point-wise initial states in conservative variables ``(rho, m1, m2, E)``
   for the isentropic vortex, the Sedov-type blast, the 60-degree double Mach
-  reflection and the four-quadrant Riemann problem.
+  reflection and the four-quadrant Riemann problem;
+* near-equilateral lattice triangulations of non-rectangular domains (the
+  paper's forward-facing-step tunnel and 30-degree wedge) with their
+  boundary conditions.
 
 Projection of a point-wise state onto the modal basis is method arithmetic
 and lives on each side of the boundary separately.
@@ -140,6 +143,127 @@ def jittered_grid(nx: int, ny: int, box=(0.0, 1.0, 0.0, 1.0), seed: int = 0,
                     bc[sel, e] = tag
     return Mesh(xy=xy, tri=tri, canon=canon, bc=bc, nx=nx, ny=ny, box=tuple(box),
                 meta={"seed": seed, "jitter": jitter, "periodic": periodic})
+
+
+# ----------------------------------------------------------------------------
+# Near-equilateral lattice triangulations of non-rectangular domains
+# ----------------------------------------------------------------------------
+
+def _lattice_row(x0, x1, h, offset, required, rng, jitter):
+    """Sorted x positions of one row on [x0, x1]: the end points, the required
+    points, and the lattice points j h + offset at least 0.7 h away from them,
+    each moved by U(-jitter, jitter) h."""
+    fixed = sorted({x0, x1, *[r for r in required if x0 <= r <= x1]})
+    cand = offset + h * np.arange(math.ceil((x0 - offset) / h), math.floor((x1 - offset) / h) + 1)
+    keep = np.ones(cand.shape, bool)
+    for f in fixed:
+        keep &= np.abs(cand - f) > 0.7 * h
+    cand = cand[keep] + rng.uniform(-jitter, jitter, int(keep.sum())) * h
+    return np.unique(np.concatenate([np.asarray(fixed, dtype=np.float64), cand]))
+
+
+def _rows(y0, y1, dy):
+    n = max(1, int(round((y1 - y0) / dy)))
+    return [y0 + (y1 - y0) * r / n for r in range(n + 1)]
+
+
+def lattice_mesh(ys, spans, strips, h, seed=0, jitter=0.1, required=(), classify=None) -> Mesh:
+    """Triangulation of a domain swept by horizontal rows of points.
+
+    Row r lies at height ``ys[r]`` and spans ``spans[r] = (x0, x1)``; its
+    points are a lattice of spacing ``h`` shifted by h/2 on odd rows (so the
+    triangles are close to equilateral when the row spacing is about
+    h sqrt(3)/2), plus the span's end points and the ``required`` (x, y)
+    points on that row.  The strip between rows r and r+1 joins the points of
+    row r within ``strips[r][0]`` and those of row r+1 within ``strips[r][1]``
+    (x-ranges) by a zipper: walking left to right, the next triangle takes the
+    next point of whichever row has the smaller x.  Boundary edges (used by
+    one triangle) get ``classify(pa, pb) -> tag``.
+    """
+    rng = np.random.default_rng(seed)
+    rows, base, pts = [], [], []
+    for r, y in enumerate(ys):
+        req = [x for (x, yy) in required if abs(yy - y) < 1e-12]
+        xs = _lattice_row(spans[r][0], spans[r][1], h, 0.5 * h * (r % 2), req, rng, jitter)
+        base.append(sum(len(q) for q in rows))
+        rows.append(xs)
+        pts.append(np.stack([xs, np.full(xs.shape, y)], axis=1))
+    xy = np.concatenate(pts).astype(np.float64)
+    tris = []
+    for r in range(len(ys) - 1):
+        (aL, bL), (aU, bU) = strips[r]
+        xl, xu = rows[r], rows[r + 1]
+        lo = base[r] + np.nonzero((xl >= aL - 1e-12) & (xl <= bL + 1e-12))[0]
+        up = base[r + 1] + np.nonzero((xu >= aU - 1e-12) & (xu <= bU + 1e-12))[0]
+        xlo, xup = xy[lo, 0], xy[up, 0]
+        i = j = 0
+        nl, nu = len(lo) - 1, len(up) - 1
+        out = []
+        while i < nl or j < nu:
+            if j == nu or (i < nl and xlo[i + 1] <= xup[j + 1]):
+                out.append((lo[i], lo[i + 1], up[j]))   # counter-clockwise: lower edge, then up
+                i += 1
+            else:
+                out.append((lo[i], up[j + 1], up[j]))
+                j += 1
+        tris.append(np.asarray(out, dtype=np.int64))
+    tri = np.concatenate(tris).astype(np.int32)
+    # boundary edges: edges used by one triangle
+    bc = np.zeros(tri.shape, dtype=np.int8)
+    a = tri[:, [1, 2, 0]].reshape(-1).astype(np.int64)
+    b = tri[:, [2, 0, 1]].reshape(-1).astype(np.int64)
+    key = np.minimum(a, b) * xy.shape[0] + np.maximum(a, b)
+    _, inv, cnt = np.unique(key, return_inverse=True, return_counts=True)
+    once = np.nonzero(cnt[inv] == 1)[0]
+    tags = np.asarray([classify(xy[a[e]], xy[b[e]]) for e in once], dtype=np.int8)
+    bc.reshape(-1)[once] = tags
+    return Mesh(xy=xy, tri=tri, canon=np.arange(xy.shape[0], dtype=np.int32), bc=bc,
+                box=(min(s[0] for s in spans), max(s[1] for s in spans), ys[0], ys[-1]),
+                meta={"seed": seed, "jitter": jitter, "h": h, "lattice": True})
+
+
+def ffs_mesh(h=1.0 / 112, seed=21):
+    """Wind tunnel [0, 3] x [0, 1] with a step of height 0.2 from x = 0.6
+    (Sec. 5, flow past a forward facing step): inflow (constant state 0) at
+    x = 0, outflow at x = 3, reflecting walls elsewhere."""
+    dy = h * math.sqrt(3.0) / 2.0
+    lo, hi = _rows(0.0, 0.2, dy), _rows(0.2, 1.0, dy)
+    ys = lo + hi[1:]
+    nlo = len(lo) - 1
+    spans = [(0.0, 0.6) if r < nlo else (0.0, 3.0) for r in range(len(ys))]
+    strips = [((0.0, 0.6), (0.0, 0.6)) if r < nlo else ((0.0, 3.0), (0.0, 3.0)) for r in range(len(ys) - 1)]
+
+    def classify(pa, pb):
+        if pa[0] == 0.0 and pb[0] == 0.0:
+            return BC_DIRICHLET0
+        if pa[0] == 3.0 and pb[0] == 3.0:
+            return BC_TRANSMISSIVE
+        return BC_REFLECT
+    return lattice_mesh(ys, spans, strips, h, seed=seed, required=[(0.6, 0.2)], classify=classify)
+
+
+def wedge_mesh(h=1.0 / 320, seed=22, x_wedge=0.1, length=2.8, height=2.0):
+    """Tube [0, length] x [0, height] over a 30-degree wedge rising from
+    (x_wedge, 0) (Sec. 5, double Mach reflection): inflow (constant state 0)
+    at x = 0, outflow at x = length, the moving-shock exact solution on the top
+    and on the bottom segment before the wedge, reflection on the wedge."""
+    dy = h * math.sqrt(3.0) / 2.0
+    s3 = math.sqrt(3.0)
+    yc = (length - x_wedge) / s3                       # where the wedge meets the outflow side
+    ys = _rows(0.0, yc, dy) + _rows(yc, height, dy)[1:]
+    xe = lambda y: min(length, x_wedge + y * s3)
+    spans = [(0.0, xe(y)) for y in ys]
+    strips = [((0.0, xe(ys[r])), (0.0, xe(ys[r + 1]))) for r in range(len(ys) - 1)]
+
+    def classify(pa, pb):
+        if pa[0] == 0.0 and pb[0] == 0.0:
+            return BC_DIRICHLET0
+        if pa[0] == length and pb[0] == length:
+            return BC_TRANSMISSIVE
+        if (pa[1] == height and pb[1] == height) or (pa[1] == 0.0 and pb[1] == 0.0):
+            return BC_SHOCK
+        return BC_REFLECT
+    return lattice_mesh(ys, spans, strips, h, seed=seed, classify=classify)
 
 
 # ----------------------------------------------------------------------------
@@ -294,6 +418,39 @@ def uniform_workload(n=16, k=2, seed=5, state=(1.0, 0.3, -0.2, 2.5), periodic=Tr
     st = np.asarray(state, dtype=np.float64)
     return Workload(name=f"uniform{n}_P{k}", mesh=mesh, k=k, t_end=0.1,
                     u0=lambda x, y: np.broadcast_to(st, np.shape(x) + (4,)).copy())
+
+
+def ffs_workload(h=1.0 / 112, k=2, seed=21, t_end=4.0):
+    """Mach 3 flow past a forward facing step (Sec. 5): uniform
+    (rho, v1, v2, p) = (1.4, 3, 0, 1), which is also the inflow state.  The
+    paper's mesh (73,862 cells, h = 1/80 refined to 1/320 near the corner) is
+    not available; the default h = 1/112 gives a uniform lattice mesh of about
+    the same cell count."""
+    mesh = ffs_mesh(h, seed)
+    inflow = prim_to_cons(1.4, 3.0, 0.0, 1.0).reshape(4)
+    bc_state = np.zeros((4, 4))
+    bc_state[0] = inflow
+    return Workload(name=f"ffs_h{round(1.0 / h)}_P{k}", mesh=mesh, k=k, t_end=t_end,
+                    u0=lambda x, y: np.broadcast_to(inflow, np.shape(x) + (4,)).copy(), bc_state=bc_state)
+
+
+def wedge_dmr_workload(h=1.0 / 320, k=2, seed=22, t_end=0.2):
+    """Double Mach reflection in a tube over a 30-degree wedge (Sec. 5): a
+    Mach-10 shock at x = 0.1 moving right, post-shock (8, 8.25, 0, 116.5)
+    behind it and (1.4, 0, 0, 1) ahead.  The default h = 1/320 gives about the
+    paper's 828,840 cells."""
+    mesh = wedge_mesh(h, seed)
+    post = prim_to_cons(8.0, 8.25, 0.0, 116.5).reshape(4)
+    pre = prim_to_cons(1.4, 0.0, 0.0, 1.0).reshape(4)
+    bc_state = np.zeros((4, 4))
+    bc_state[0] = post
+    bc_state[1] = pre
+
+    def u0(x, y):
+        x = np.asarray(x, dtype=np.float64)
+        return np.where((x <= 0.1)[..., None], post, pre)
+    return Workload(name=f"wedge_dmr_h{round(1.0 / h)}_P{k}", mesh=mesh, k=k, t_end=t_end, u0=u0,
+                    bc_state=bc_state, shock=(0.1, math.pi / 2.0, 10.0, 1, 0))
 
 
 def random_modal_state(nt: int, k: int, seed: int, mean=(1.0, 0.2, -0.1, 2.5),

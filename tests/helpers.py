@@ -98,3 +98,16 @@ def rotate_mesh_state(mesh, u, phi):
     ur[1] = c * u[1] - s * u[2]
     ur[2] = s * u[1] + c * u[2]
     return xy, ur
+
+
+def rel_err(a, b):
+    """Largest error of a against the oracle result b, relative to the largest
+    oracle magnitude of each conserved quantity: density, energy, and the
+    momentum vector, whose two components share one scale (the scheme is
+    rotation invariant, so a flow along x must not be judged by the round-off
+    of its tiny y-momentum alone)."""
+    import numpy as np
+    mag = np.abs(b).reshape(4, -1).max(1)
+    mag[1] = mag[2] = max(mag[1], mag[2])
+    scale = np.maximum(mag, 1e-300)
+    return float((np.abs(a - b).reshape(4, -1).max(1) / scale).max())

@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 from paper_2409_09620_gb300 import workloads as W
+from tests.helpers import rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -20,11 +21,6 @@ def N():
     from paper_2409_09620_gb300 import native
     native.lib()
     return native
-
-
-def rel_err(a, b):
-    scale = np.maximum(np.abs(b).reshape(4, -1).max(1), 1e-300)
-    return float((np.abs(a - b).reshape(4, -1).max(1) / scale).max())
 
 
 def _solvers(oracle_mod, N, wl):
