@@ -1,4 +1,4 @@
-"""Compile the oracle's C source into ``oracle/liboracle.so`` (gcc, OpenMP)."""
+"""Compile the oracle's C sources into ``oracle/liboracle.so`` (gcc, OpenMP)."""
 from __future__ import annotations
 
 import os
@@ -6,16 +6,16 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SRC = os.path.join(HERE, "oracle.c")
+SRCS = [os.path.join(HERE, f) for f in ("oracle.c", "scalar.c")]
+DEPS = SRCS + [os.path.join(HERE, f) for f in ("oracle.h", "oracle_mesh.h")]
 LIB = os.path.join(HERE, "liboracle.so")
 
 
 def build(force: bool = False) -> str:
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= max(
-            os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "oracle.h"))):
+    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= max(os.path.getmtime(f) for f in DEPS):
         return LIB
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
-           "-Wall", "-Wno-unused-function", "-o", LIB + ".tmp", SRC, "-lm"]
+           "-Wall", "-Wno-unused-function", "-o", LIB + ".tmp", *SRCS, "-lm"]
     subprocess.check_call(cmd)
     os.replace(LIB + ".tmp", LIB)
     return LIB

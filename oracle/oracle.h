@@ -112,6 +112,41 @@ int or_advance(const or_mesh *m, const or_config *cf, double *u, double *t, doub
                int64_t max_steps, int64_t *counters);
 int or_num_threads(void);
 
+/* ------------------------------------------------------------------------ */
+/* Scalar conservation laws u_t + div F(u) = 0, P1-P3 OEDG (Sec. 2; scalar.c)
+ * State layout: u[l * nt + K], nb = (k + 1)(k + 2) / 2 modes.               */
+/* ------------------------------------------------------------------------ */
+typedef struct or_sc_config {
+  int32_t k;          /* 1, 2 or 3 */
+  int32_t flux;       /* 0: linear F = (ax u, ay u); 1: Burgers F = (u^2/2, u^2/2) */
+  int32_t oe;         /* 0 off, 1 OE procedure after every stage (eq. oe:scalar) */
+  int32_t rk;         /* 2: SSP-RK(2,2); 3: SSP-RK(3,3) (eq. RKTime) */
+  double ax, ay;      /* velocity of the linear flux */
+  double cfl;         /* multiplies the time step of Sec. 5 */
+  double bc_state[4]; /* values of the constant-state boundary tags 3..6 */
+} or_sc_config;
+
+/* d^(r+s) Psi_l / d xi^r d eta^s at (xi, eta), l = 0..9 (eq. basisfunc) */
+void or_sc_basis(double xi, double eta, int r, int s, double *out10);
+void or_sc_mass_constants(int k, double *c);
+double or_sc_eval(const or_mesh *m, int k, const double *u, int64_t K, double x, double y);
+/* physical derivative d^(p+q) u / dx^p dy^q of cell K's polynomial at (x, y) */
+double or_sc_deriv(const or_mesh *m, int k, const double *u, int64_t K, double x, double y, int p, int q);
+/* vals[K * 12 + mu]: values at the 12-point rule's points (or_quad12_points) */
+int or_sc_project(const or_mesh *m, int k, const double *vals, double *coeffs);
+double or_sc_alpha(const or_mesh *m, const or_sc_config *cf, const double *u);
+int or_sc_L(const or_mesh *m, const or_sc_config *cf, const double *u, double alpha, double *L);
+/* stats[0] = domain mean, stats[1] = sup |u - mean| at the volume points, stats[2] = |Omega| */
+void or_sc_stats(const or_mesh *m, const or_sc_config *cf, const double *u, double *stats);
+/* OE procedure; sigma (nullable) receives sigma[j * nt + K], j = 0..k */
+int or_sc_oe(const or_mesh *m, const or_sc_config *cf, const double *u, double dt, const double *stats,
+             double *out, double *sigma);
+/* min_K |K| / ((2k + 1) sum_i l_K^(i)) */
+double or_sc_dt_base(const or_mesh *m, int k);
+int or_sc_step(const or_mesh *m, const or_sc_config *cf, double *u, double *t, double t_end, double *dt_out);
+int or_sc_advance(const or_mesh *m, const or_sc_config *cf, double *u, double *t, double t_end,
+                  int64_t max_steps, int64_t *steps);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,6 +23,39 @@ class Config(C.Structure):
                 ("shock_pre", C.c_int32), ("shock_post", C.c_int32)]
 
 
+class ScConfig(C.Structure):
+    _fields_ = [("k", C.c_int32), ("flux", C.c_int32), ("oe", C.c_int32), ("rk", C.c_int32),
+                ("ax", C.c_double), ("ay", C.c_double), ("cfl", C.c_double), ("bc_state", C.c_double * 4)]
+
+
+def make_sc_config(k, flux=0, oe=1, rk=None, ax=1.0, ay=1.0, cfl=1.0, bc_state=(0.0, 0.0, 0.0, 0.0)):
+    """Scalar OEDG configuration; rk defaults to SSP-RK(2,2) for P1 and
+    SSP-RK(3,3) otherwise (Sec. 5)."""
+    cf = ScConfig()
+    cf.k, cf.flux, cf.oe = k, flux, oe
+    cf.rk = (2 if k == 1 else 3) if rk is None else rk
+    cf.ax, cf.ay, cf.cfl = ax, ay, cfl
+    for i in range(4):
+        cf.bc_state[i] = float(bc_state[i])
+    return cf
+
+
+def sc_nb(k):
+    return (k + 1) * (k + 2) // 2
+
+
+def sc_basis(xi, eta, r=0, s=0):
+    out = np.empty(10)
+    lib().or_sc_basis(float(xi), float(eta), r, s, _p(out))
+    return out
+
+
+def sc_mass_constants(k):
+    c = np.empty(10)
+    lib().or_sc_mass_constants(k, _p(c))
+    return c[: sc_nb(k)]
+
+
 def lib():
     global _lib
     if _lib is None:
@@ -52,6 +85,18 @@ def lib():
         L.or_step.argtypes = [P, P, P, P, dbl, P, P]
         L.or_advance.argtypes = [P, P, P, P, dbl, i64, P]
         L.or_num_threads.restype = C.c_int
+        L.or_sc_basis.argtypes = [dbl, dbl, C.c_int, C.c_int, P]
+        L.or_sc_mass_constants.argtypes = [C.c_int, P]
+        L.or_sc_eval.argtypes = [P, C.c_int, P, i64, dbl, dbl]; L.or_sc_eval.restype = dbl
+        L.or_sc_deriv.argtypes = [P, C.c_int, P, i64, dbl, dbl, C.c_int, C.c_int]; L.or_sc_deriv.restype = dbl
+        L.or_sc_project.argtypes = [P, C.c_int, P, P]
+        L.or_sc_alpha.argtypes = [P, P, P]; L.or_sc_alpha.restype = dbl
+        L.or_sc_L.argtypes = [P, P, P, dbl, P]
+        L.or_sc_stats.argtypes = [P, P, P, P]
+        L.or_sc_oe.argtypes = [P, P, P, dbl, P, P, P]
+        L.or_sc_dt_base.argtypes = [P, C.c_int]; L.or_sc_dt_base.restype = dbl
+        L.or_sc_step.argtypes = [P, P, P, P, dbl, P]
+        L.or_sc_advance.argtypes = [P, P, P, P, dbl, i64, P]
         _lib = L
     return _lib
 
@@ -223,6 +268,66 @@ class OracleMesh:
         cnt = np.zeros(4, np.int64)
         rc = lib().or_advance(self.h, C.byref(cf), _p(u), _p(tt), t_end, max_steps, _p(cnt))
         return u, float(tt[0]), cnt, rc
+
+
+    # -- scalar conservation laws (Sec. 2) ------------------------------------
+    def sc_project(self, k, fn):
+        """L2 projection of a point-wise scalar fn(x, y) -> [...] (12-point rule)."""
+        xy = self.quad12_points()
+        vals = np.ascontiguousarray(np.asarray(fn(xy[..., 0], xy[..., 1]), dtype=np.float64).reshape(self.nt, 12))
+        u = np.empty((sc_nb(k), self.nt))
+        rc = lib().or_sc_project(self.h, k, _p(vals), _p(u))
+        if rc != 0:
+            raise ValueError(rc)
+        return u
+
+    def sc_eval(self, k, u, K, x, y):
+        return lib().or_sc_eval(self.h, k, _p(np.ascontiguousarray(u)), K, x, y)
+
+    def sc_deriv(self, k, u, K, x, y, p, q):
+        return lib().or_sc_deriv(self.h, k, _p(np.ascontiguousarray(u)), K, x, y, p, q)
+
+    def sc_alpha(self, cf, u):
+        return lib().or_sc_alpha(self.h, C.byref(cf), _p(np.ascontiguousarray(u)))
+
+    def sc_L(self, cf, u, alpha):
+        L = np.empty_like(np.ascontiguousarray(u))
+        rc = lib().or_sc_L(self.h, C.byref(cf), _p(np.ascontiguousarray(u)), alpha, _p(L))
+        if rc != 0:
+            raise ValueError(rc)
+        return L
+
+    def sc_stats(self, cf, u):
+        st = np.empty(3)
+        lib().or_sc_stats(self.h, C.byref(cf), _p(np.ascontiguousarray(u)), _p(st))
+        return st
+
+    def sc_oe(self, cf, u, dt, stats=None, want_sigma=False):
+        u = np.ascontiguousarray(u)
+        st = self.sc_stats(cf, u) if stats is None else np.ascontiguousarray(stats, dtype=np.float64)
+        out = np.empty_like(u)
+        sig = np.empty((cf.k + 1, self.nt)) if want_sigma else None
+        rc = lib().or_sc_oe(self.h, C.byref(cf), _p(u), dt, _p(st), _p(out), _p(sig))
+        if rc != 0:
+            raise ValueError(rc)
+        return (out, sig) if want_sigma else out
+
+    def sc_dt_base(self, k):
+        return lib().or_sc_dt_base(self.h, k)
+
+    def sc_step(self, cf, u, t, t_end):
+        u = np.ascontiguousarray(u).copy()
+        tt = np.array([t], dtype=np.float64)
+        dt = np.zeros(1)
+        rc = lib().or_sc_step(self.h, C.byref(cf), _p(u), _p(tt), t_end, _p(dt))
+        return u, float(tt[0]), float(dt[0]), rc
+
+    def sc_advance(self, cf, u, t, t_end, max_steps=1 << 60):
+        u = np.ascontiguousarray(u).copy()
+        tt = np.array([t], dtype=np.float64)
+        st = np.zeros(1, np.int64)
+        rc = lib().or_sc_advance(self.h, C.byref(cf), _p(u), _p(tt), t_end, max_steps, _p(st))
+        return u, float(tt[0]), int(st[0]), rc
 
 
 def basis(xi, eta):

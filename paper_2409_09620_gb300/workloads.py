@@ -266,6 +266,101 @@ def wedge_mesh(h=1.0 / 320, seed=22, x_wedge=0.1, length=2.8, height=2.0):
     return lattice_mesh(ys, spans, strips, h, seed=seed, classify=classify)
 
 
+def refine_mesh(mesh: Mesh) -> Mesh:
+    """Split every triangle into four through its edge midpoints (the paper's
+    refinement of its scalar meshes, Sec. 5).  Midpoints of the two copies of
+    a periodic edge are identified through ``canon``; boundary edges keep
+    their tags on both halves."""
+    xy = [tuple(p) for p in mesh.xy]
+    canon = list(mesh.canon)
+    mids, cmid = {}, {}
+
+    def mid(a, b):
+        key = (min(a, b), max(a, b))
+        if key not in mids:
+            mids[key] = len(xy)
+            xy.append(tuple(0.5 * (mesh.xy[a] + mesh.xy[b])))
+            ck = (min(mesh.canon[a], mesh.canon[b]), max(mesh.canon[a], mesh.canon[b]))
+            canon.append(cmid.setdefault(ck, mids[key]))
+        return mids[key]
+    tri, bc = [], []
+    for (a, b, c), (ta, tb, tc) in zip(mesh.tri, mesh.bc):
+        ma, mb, mc = mid(b, c), mid(c, a), mid(a, b)
+        tri += [(a, mc, mb), (mc, b, ma), (mb, ma, c), (ma, mb, mc)]
+        bc += [(0, tb, tc), (ta, 0, tc), (ta, tb, 0), (0, 0, 0)]
+    return Mesh(xy=np.asarray(xy, dtype=np.float64), tri=np.asarray(tri, dtype=np.int32),
+                canon=np.asarray(canon, dtype=np.int32), bc=np.asarray(bc, dtype=np.int8),
+                box=mesh.box, meta={**mesh.meta, "refined": mesh.meta.get("refined", 0) + 1})
+
+
+def scalar_mesh(level: int, n0: int = 5, seed: int = 31) -> Mesh:
+    """Periodic unit square: a jittered n0 x n0 grid (2 n0^2 = 50 cells, about
+    the paper's 44-cell coarsest mesh) refined ``level`` times."""
+    m = jittered_grid(n0, n0, (0.0, 1.0, 0.0, 1.0), seed=seed, periodic=True)
+    for _ in range(level):
+        m = refine_mesh(m)
+    return m
+
+
+def linear_smooth(x, y, t=0.0):
+    """u_t + u_x + u_y = 0 from sin(2 pi (x + y)) (Sec. 5, smooth linear problem)."""
+    return np.sin(2.0 * np.pi * (np.asarray(x) + np.asarray(y) - 2.0 * t))
+
+
+def burgers_smooth(x, y, t=0.0, iters=60):
+    """u_t + (u^2/2)_x + (u^2/2)_y = 0 from 0.5 sin(2 pi (x + y)) (Sec. 5),
+    exact while smooth (t < 1 / (2 pi)): u = 0.5 sin(2 pi (x + y - 2 u t)),
+    solved by Newton's method along the characteristics."""
+    s = np.asarray(x, dtype=np.float64) + np.asarray(y, dtype=np.float64)
+    u = 0.5 * np.sin(2.0 * np.pi * s)
+    for _ in range(iters):
+        ph = 2.0 * np.pi * (s - 2.0 * u * t)
+        g = u - 0.5 * np.sin(ph)
+        u = u - g / (1.0 + 2.0 * np.pi * t * np.cos(ph))
+    return u
+
+
+@dataclass
+class ScalarWorkload:
+    name: str
+    mesh: Mesh
+    k: int
+    flux: int                  # 0 linear (velocity (1, 1)), 1 Burgers
+    t_end: float
+    u0: object                 # callable (x, y) -> values
+    exact: object = None       # callable (x, y, t) -> values, where known
+    bc_state: tuple = (0.0, 0.0, 0.0, 0.0)
+
+
+def scalar_linear_workload(level=3, k=2):
+    return ScalarWorkload(name=f"linear_L{level}_P{k}", mesh=scalar_mesh(level), k=k, flux=0, t_end=0.1,
+                          u0=lambda x, y: linear_smooth(x, y), exact=linear_smooth)
+
+
+def scalar_burgers_workload(level=3, k=2):
+    return ScalarWorkload(name=f"burgers_L{level}_P{k}", mesh=scalar_mesh(level), k=k, flux=1, t_end=0.05,
+                          u0=lambda x, y: burgers_smooth(x, y), exact=burgers_smooth)
+
+
+def burgers_riemann2_workload(n=64, k=2, seed=32):
+    """Burgers Riemann problem II (Sec. 5): 2 for x, y < 0.25, 3 for x, y >=
+    0.25, 1 elsewhere; inflow (the initial values) on the left and bottom
+    sides, outflow on the right and top, to t = 1/12."""
+    inflow = lambda x, y: BC_DIRICHLET0 if (x < 0.25 and y < 0.25) else BC_DIRICHLET0 + 1
+    mesh = jittered_grid(n, n, (0.0, 1.0, 0.0, 1.0), seed=seed,
+                         side_tags={"left": lambda x, y: BC_DIRICHLET0 if y < 0.25 else BC_DIRICHLET0 + 1,
+                                    "bottom": lambda x, y: BC_DIRICHLET0 if x < 0.25 else BC_DIRICHLET0 + 1,
+                                    "right": BC_TRANSMISSIVE, "top": BC_TRANSMISSIVE})
+    del inflow
+
+    def u0(x, y):
+        x = np.asarray(x, dtype=np.float64)
+        y = np.asarray(y, dtype=np.float64)
+        return np.where((x < 0.25) & (y < 0.25), 2.0, np.where((x >= 0.25) & (y >= 0.25), 3.0, 1.0))
+    return ScalarWorkload(name=f"burgers_rm2_{n}_P{k}", mesh=mesh, k=k, flux=1, t_end=1.0 / 12.0, u0=u0,
+                          bc_state=(2.0, 1.0, 0.0, 0.0))
+
+
 # ----------------------------------------------------------------------------
 # Point-wise initial states (conservative variables), vectorised over points.
 # ----------------------------------------------------------------------------
