@@ -304,6 +304,53 @@ int32_t dg_stats_noalloc(const dg_mesh *mesh, int32_t k, const double *coeffs, d
                          void *cuda_stream);
 
 /* thread-local message of the last error */
+/* ---------------------------------------------------------------------- */
+/* Scalar conservation laws u_t + div F(u) = 0: the OEDG scheme of Sec. 2   */
+/* (DG operator eq. DGScalar:Dis with the LF flux eq. fluxLF; OE procedure  */
+/* eqs. oe:scalar, OEScalar:Coef1, OEScalar:beta, OEScalar:Coef2; SSP-RK    */
+/* eq. RKTime; the time step of Sec. 5), P1-P3, FP64, on any dg_mesh whose  */
+/* boundary edges are transmissive or constant-state (tags 2..6).            */
+/* State layout: coeffs[l * nt + K], l = 0..nb-1, nb = (k+1)(k+2)/2 modes of */
+/* the basis eq. basisfunc (Psi^(0..9)).                                    */
+/* ---------------------------------------------------------------------- */
+#define DG_FLUX_LINEAR 0   /* F(u) = (ax u, ay u) */
+#define DG_FLUX_BURGERS 1  /* F(u) = (u^2 / 2, u^2 / 2) */
+
+typedef struct dg_scalar_config {
+  int32_t k;          /* 1, 2 or 3 */
+  int32_t flux;       /* DG_FLUX_LINEAR or DG_FLUX_BURGERS */
+  int32_t oe;         /* 1: OE procedure after every stage; 0: plain RKDG */
+  int32_t rk;         /* 2: SSP-RK(2,2), 3: SSP-RK(3,3) (both C_SSP = 1) */
+  double ax, ay;      /* velocity of the linear flux */
+  double cfl;         /* dt = cfl / alpha * min_K |K| / ((2k+1) sum_i l_K^(i)) (Sec. 5; 1 = paper) */
+  double bc_state[4]; /* values of the constant-state boundary tags 3..6 */
+} dg_scalar_config;
+
+typedef struct dg_scalar dg_scalar;
+
+/* L2 projection of point values vals[K * 12 + mu] at the 12-point rule's
+ * points (dg_quad_points) onto P^k, k = 1..3 (host). */
+int32_t dg_scalar_project(const dg_mesh *mesh, int32_t k, const double *vals, double *coeffs);
+/* New solver on the device; coeffs are used as given (host, nb * nt doubles).
+ * alpha^LF is the maximum of |F'(u) . n| over the edge Gauss points and both
+ * traces of each stage input.  DG_EINVAL for a bad configuration or a
+ * boundary tag other than 2..6. */
+int32_t dg_scalar_init(const dg_mesh *mesh, const dg_scalar_config *cfg, const double *coeffs, void *cuda_stream,
+                       dg_scalar **out);
+/* Steps until t_end (the last step clamped) or max_steps; stats may be NULL
+ * (steps, t, dt_last, alpha are filled).  DG_ENONPHYS if the state stops
+ * being finite. */
+int32_t dg_scalar_advance(dg_scalar *solver, double t_end, int64_t max_steps, dg_stats *stats);
+/* Enqueue n steps (t_end = +inf) without synchronising. */
+int32_t dg_scalar_advance_async(dg_scalar *solver, int64_t n);
+void *dg_scalar_stream(const dg_scalar *solver);
+int32_t dg_scalar_get_state(const dg_scalar *solver, double *coeffs, size_t len, double *t);
+/* L1, L2 and L-infinity errors of the current state against exact values
+ * exact[K * 12 + mu] at the 12-point rule's points (dg_quad_points), the
+ * norms integrated with that rule: out3 = (L1, L2, Linf). */
+int32_t dg_scalar_errors(const dg_scalar *solver, const double *exact, double *out3);
+void dg_scalar_destroy(dg_scalar *solver);
+
 const char *dg_last_error(void);
 
 #ifdef __cplusplus

@@ -50,6 +50,7 @@ struct dg_mesh {
   std::vector<int32_t> nbr, nbr_edge;   // host adjacency
   std::vector<double> quad_xy;          // lazily built 12-point rule points
   std::vector<double> vxy_host;         // [6][nt]
+  std::vector<int8_t> bnd_tag;          // [3 nt] tag of each boundary edge (0 for interior edges)
   // device
   double *area = nullptr, *jinv = nullptr, *nrm = nullptr, *len = nullptr, *vxy = nullptr, *node = nullptr,
          *c_area = nullptr, *hgeo = nullptr;
@@ -180,10 +181,12 @@ extern "C" int32_t dg_mesh_create(int64_t nv, const double *xy, int64_t nt, cons
     }
     e = f;
   }
+  m->bnd_tag.assign((size_t)(3 * nt), 0);
   for (int64_t K = 0; K < nt; ++K)
     for (int i = 0; i < 3; ++i) {
       const int32_t nbK = m->nbr[3 * K + i];
       conn[(size_t)i * nt + K] = nbK >= 0 ? ((nbK << 2) | m->nbr_edge[3 * K + i]) : -(int32_t)bc[3 * K + i];
+      if (nbK < 0) m->bnd_tag[3 * K + i] = bc[3 * K + i];
     }
   // edge list: every edge once, owned by its lower cell id (or its only cell),
   // ordered by owner; tiles of TPB cells own contiguous edge ranges
@@ -561,7 +564,11 @@ extern "C" int32_t dg_init(const dg_mesh *mesh, const dg_config *cfg, const doub
     delete s;
     return rc;
   }
-  // capture one time step as a CUDA graph
+  // capture one time step as a CUDA graph (with stack room for its kernels)
+  if ((rc = ensure_stack_limit(stage_kernels_local_bytes(cfg->k, cfg->precision))) != DG_OK) {
+    delete s;
+    return rc;
+  }
   cudaGraph_t graph = nullptr;
   STRY(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
   enqueue_step(s);
@@ -836,4 +843,27 @@ void solver_states(const dg_solver *s, StateBuf *un, StateBuf *uh, StateBuf *us)
 int solver_nb(const dg_solver *s) { return s->nb; }
 int32_t solver_read_scalars(const dg_solver *s, Scalars *h) { return read_scalars(s, h); }
 int32_t solver_write_scalars(dg_solver *s, const Scalars *h) { return write_scalars(s, h); }
+
+int32_t ensure_stack_limit(size_t bytes) {
+  size_t cur = 0;
+  cudaError_t e = cudaDeviceGetLimit(&cur, cudaLimitStackSize);
+  if (e == cudaSuccess && cur < bytes) e = cudaDeviceSetLimit(cudaLimitStackSize, bytes);
+  if (e != cudaSuccess) return set_error(DG_ECUDA, cudaGetErrorString(e));
+  return DG_OK;
+}
+
+MeshDev mesh_device_view(const dg_mesh *m) {
+  return MeshDev{m->nt,   m->area,   m->jinv,  m->nrm,   m->len,    m->vxy,    m->node,  m->hgeo, m->limv,
+                 m->conn, m->ne,     m->e_cell, m->e_loc, m->etile, m->cedge, m->jinv_f, m->nrm_f, m->len_f,
+                 m->hgeo_f, m->iarea};
+}
+
+// every boundary edge carries a tag the scalar solver handles (transmissive or
+// constant state), or any tag for the Euler solver
+bool mesh_boundary_tags_ok(const dg_mesh *m, int scalar) {
+  if (!scalar) return true;
+  for (int8_t t : m->bnd_tag)
+    if (t != 0 && !(t == DG_BC_TRANSMISSIVE || (t >= DG_BC_DIRICHLET0 && t < DG_BC_DIRICHLET0 + 4))) return false;
+  return true;
+}
 }  // namespace dg

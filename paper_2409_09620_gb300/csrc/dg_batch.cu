@@ -278,6 +278,10 @@ struct BatchCore {
     if (exec) { cudaGraphExecDestroy(exec); exec = nullptr; }
     graph_ok = false;
     if (host_sv.empty()) return DG_OK;
+    const size_t stack = prec == DG_PREC_MIXED ? kernel_local_bytes(k_batch_stage<float>)
+                                               : kernel_local_bytes(k_batch_stage<double>);
+    int32_t rc = ensure_stack_limit(stack);
+    if (rc != DG_OK) return rc;
     cudaGraph_t g = nullptr;
     if (cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
       cudaError_t e = cudaSuccess;

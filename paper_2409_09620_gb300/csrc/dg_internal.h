@@ -62,6 +62,25 @@ int solver_nb(const dg_solver *s);
 int32_t solver_read_scalars(const dg_solver *s, Scalars *h);
 int32_t solver_write_scalars(dg_solver *s, const Scalars *h);
 
+// the mesh's device arrays as the kernels see them; boundary tags usable by
+// the scalar solver (dg_api.cu)
+MeshDev mesh_device_view(const dg_mesh *m);
+bool mesh_boundary_tags_ok(const dg_mesh *m, int scalar);
+
+// Raise the context's per-thread stack limit to at least `bytes` (it is never
+// lowered).  The driver grows the stack for a plain kernel launch on its own;
+// this makes sure kernels replayed from a CUDA graph find the same room
+// (dg_api.cu).
+int32_t ensure_stack_limit(size_t bytes);
+// local (stack) bytes per thread a kernel needs, 0 if it cannot be queried
+template <typename F>
+size_t kernel_local_bytes(F *fn) {
+  cudaFuncAttributes a{};
+  return cudaFuncGetAttributes(&a, reinterpret_cast<const void *>(fn)) == cudaSuccess ? a.localSizeBytes : 0;
+}
+// the largest of the per-stage kernels of the given degree and precision (dg_kernels.cu)
+size_t stage_kernels_local_bytes(int k, int prec);
+
 // mesh size, device cell areas and their host-summed total (dg_api.cu)
 void mesh_view(const dg_mesh *mesh, int64_t *nt, const double **area, double *area_total);
 // record a message for dg_last_error and return code (dg_api.cu)

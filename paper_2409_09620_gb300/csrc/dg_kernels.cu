@@ -2,6 +2,8 @@
 // BP RI-OEDG solver: mesh geometry / optimal convex decomposition, the three
 // stage kernels and the fixed-order reductions between them.
 #include "dg_internal.h"
+#include <algorithm>
+
 #include "dg_stage.cuh"
 
 namespace dg {
@@ -254,5 +256,12 @@ void launch_set_inv_normalisers(const StageCtx &c) {
 }
 
 int64_t num_blocks(int64_t nt) { return nblocks(nt); }
+
+size_t stage_kernels_local_bytes(int k, int prec) {
+  size_t n = 0;
+  DG_DISPATCH(k, prec, (n = std::max({kernel_local_bytes(k_rk<KK, Real>), kernel_local_bytes(k_stats<KK, Real>),
+                                      kernel_local_bytes(k_oe_bp<KK, Real>)})));
+  return n;
+}
 
 }  // namespace dg

@@ -45,7 +45,23 @@ class Stats(C.Structure):
 
 
 # name -> (restype, argtypes); every symbol of include/dg.h
+FLUX_LINEAR, FLUX_BURGERS = 0, 1
+
+
+class ScalarConfig(C.Structure):
+    _fields_ = [("k", i32), ("flux", i32), ("oe", i32), ("rk", i32), ("ax", dbl), ("ay", dbl), ("cfl", dbl),
+                ("bc_state", dbl * 4)]
+
+
 SIGNATURES = {
+    "dg_scalar_project": (i32, [P, i32, P, P]),
+    "dg_scalar_init": (i32, [P, P, P, P, C.POINTER(P)]),
+    "dg_scalar_advance": (i32, [P, dbl, i64, P]),
+    "dg_scalar_advance_async": (i32, [P, i64]),
+    "dg_scalar_stream": (P, [P]),
+    "dg_scalar_get_state": (i32, [P, P, C.c_size_t, C.POINTER(dbl)]),
+    "dg_scalar_errors": (i32, [P, P, P]),
+    "dg_scalar_destroy": (None, [P]),
     "dg_mesh_create": (i32, [i64, P, i64, P, P, P, C.POINTER(P)]),
     "dg_mesh_destroy": (None, [P]),
     "dg_mesh_info": (i32, [P, i32, C.POINTER(i64), C.POINTER(dbl), C.POINTER(dbl)]),
@@ -438,6 +454,78 @@ class Server:
         a, b = i64(), i64()
         _check(lib().dg_server_stats(self.h, C.byref(a), C.byref(b)))
         return dict(bytes_in_use=a.value, cell_stages_done=b.value)
+
+
+def make_scalar_config(k, flux=FLUX_LINEAR, oe=1, rk=None, ax=1.0, ay=1.0, cfl=1.0, bc_state=(0.0, 0.0, 0.0, 0.0)):
+    """Scalar OEDG configuration; rk defaults to SSP-RK(2,2) for P1 and
+    SSP-RK(3,3) otherwise."""
+    cf = ScalarConfig()
+    cf.k, cf.flux, cf.oe = k, flux, oe
+    cf.rk = (2 if k == 1 else 3) if rk is None else rk
+    cf.ax, cf.ay, cf.cfl = ax, ay, cfl
+    for i in range(4):
+        cf.bc_state[i] = float(bc_state[i])
+    return cf
+
+
+def scalar_project(mesh: Mesh, k, fn):
+    """L2 projection of a point-wise scalar fn(x, y) with the library's 12-point rule."""
+    xy = mesh.quad_points()
+    vals = np.ascontiguousarray(np.asarray(fn(xy[..., 0], xy[..., 1]), np.float64).reshape(mesh.nt, 12))
+    u = np.empty(((k + 1) * (k + 2) // 2, mesh.nt))
+    _check(lib().dg_scalar_project(mesh.h, k, _p(vals), _p(u)))
+    return u
+
+
+class ScalarSolver:
+    """dg_scalar handle: the scalar OEDG solver, state resident on the GPU."""
+
+    def __init__(self, mesh: Mesh, cfg: ScalarConfig, coeffs, stream=None):
+        self.mesh = mesh
+        self.cfg = cfg
+        self.nb = (cfg.k + 1) * (cfg.k + 2) // 2
+        u = np.ascontiguousarray(coeffs, dtype=np.float64)
+        if u.size != self.nb * mesh.nt:
+            raise ValueError("coefficient array has the wrong size")
+        h = P()
+        _check(lib().dg_scalar_init(mesh.h, C.byref(cfg), _p(u), stream, C.byref(h)))
+        self.h = h
+
+    @property
+    def stream(self):
+        return lib().dg_scalar_stream(self.h)
+
+    def advance(self, t_end, max_steps=1 << 62):
+        st = Stats()
+        _check(lib().dg_scalar_advance(self.h, t_end, max_steps, C.byref(st)))
+        return st.as_dict()
+
+    def advance_async(self, n):
+        _check(lib().dg_scalar_advance_async(self.h, n))
+
+    def get_state(self):
+        u = np.empty((self.nb, self.mesh.nt))
+        t = dbl()
+        _check(lib().dg_scalar_get_state(self.h, _p(u), u.size, C.byref(t)))
+        return u, t.value
+
+    def errors(self, exact_values):
+        """(L1, L2, Linf) against exact values [nt, 12] at the mesh's quad points."""
+        ex = np.ascontiguousarray(np.asarray(exact_values, np.float64).reshape(self.mesh.nt, 12))
+        out = np.empty(3)
+        _check(lib().dg_scalar_errors(self.h, _p(ex), _p(out)))
+        return tuple(float(v) for v in out)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().dg_scalar_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def initial_state(mesh: Mesh, workload):
