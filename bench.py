@@ -236,6 +236,7 @@ def main():
     ap.add_argument("--no-cfl-gain", action="store_true")
     ap.add_argument("--no-paper-meshes", action="store_true",
                     help="skip the forward-facing-step and wedge meshes")
+    ap.add_argument("--no-scalar", action="store_true", help="skip the scalar conservation laws")
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-rate", type=float, default=30.0)
     args = ap.parse_args()
@@ -498,6 +499,64 @@ def main():
                 del s_opt, s_zxs
             paper_meshes[key] = ent
 
+    # scalar conservation laws (Sec. 2, Sec. 5 accuracy studies): errors and
+    # orders on a mesh and its refinements, and throughput on the finest mesh
+    scalar = None
+    if not args.no_scalar:
+        from paper_2409_09620_gb300 import workloads as W
+        paper_l1 = {  # the paper's tables tab:Ex_LinearS1 and tab:Ex_BurgS1, N = 176 * 4^i
+            "linear": {"P1": [8.18e-2, 1.56e-2, 2.79e-3, 4.76e-4, 9.11e-5, 2.01e-5],
+                       "P2": [5.29e-2, 2.90e-3, 9.15e-5, 5.70e-6, 4.85e-7, 5.10e-8],
+                       "P3": [4.45e-2, 3.20e-4, 3.01e-6, 8.89e-8, 3.08e-9, 1.23e-10]},
+            "burgers": {"P1": [1.88e-2, 3.77e-3, 7.57e-4, 1.68e-4, 4.10e-5, 1.02e-5],
+                        "P2": [3.05e-3, 3.22e-4, 3.52e-5, 3.95e-6, 4.82e-7, 6.28e-8],
+                        "P3": [1.20e-3, 3.39e-5, 1.28e-6, 6.11e-8, 2.97e-9, 1.58e-10]}}
+        scalar = {"mesh": "periodic jittered 5x5 grid refined L times by quadrisection (50 * 4^L cells)",
+                  "time": "SSP-RK(2,2) for P1, SSP-RK(3,3) for P2 and P3; P3 dt scaled by (h/h_1)^(1/3)",
+                  "paper_L1": paper_l1, "paper_cells": [176, 704, 2816, 11264, 45056, 180224]}
+        levels = range(1, 6)
+        for name, make in (("linear", W.scalar_linear_workload), ("burgers", W.scalar_burgers_workload)):
+            tab = {}
+            for k in (1, 2, 3):
+                rows, prev = [], None
+                for lev in levels:
+                    wl = make(level=lev, k=k)
+                    m = N.Mesh.from_mesh(wl.mesh)
+                    u = N.scalar_project(m, k, wl.u0)
+                    cf = N.make_scalar_config(k, flux=wl.flux, cfl=0.5 ** ((lev - 1) / 3.0) if k == 3 else 1.0)
+                    sv = N.ScalarSolver(m, cf, u)
+                    st_s = sv.advance(wl.t_end)
+                    xy = m.quad_points()
+                    e = np.array(sv.errors(wl.exact(xy[..., 0], xy[..., 1], wl.t_end)))
+                    row = {"cells": wl.mesh.nt, "steps": st_s["steps"], "L1": e[0], "L2": e[1], "Linf": e[2]}
+                    if prev is not None:
+                        row["order"] = [float(v) for v in np.log2(prev / e)]
+                    rows.append(row)
+                    prev = e
+                    sv.close()
+                tab[f"P{k}"] = rows
+            scalar[name] = tab
+        thr = {}
+        wl6 = W.scalar_linear_workload(level=6, k=1)
+        m6 = N.Mesh.from_mesh(wl6.mesh)
+        for k in (1, 2, 3):
+            sv = N.ScalarSolver(m6, N.make_scalar_config(k, flux=1), N.scalar_project(m6, k, W.burgers_smooth))
+            stream = torch.cuda.ExternalStream(sv.stream)
+            sv.advance_async(5)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sv.advance_async(50)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_s = e0.elapsed_time(e1) / 50
+            stages = 2 if k == 1 else 3
+            thr[f"P{k}"] = {"ms_per_step": ms_s, "value": wl6.mesh.nt * stages / (ms_s / 1e3), "unit": UNIT,
+                            "cells": wl6.mesh.nt, "flux": "burgers"}
+            sv.close()
+        scalar["throughput"] = thr
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         wl_full = make_workload(args.workload, args.nx, args.ny)
@@ -516,7 +575,7 @@ def main():
                            "l2": "working set ~1.7 GB > 129 MB L2, no flush"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": 19 * args.steps, "clocks": clocks, "fp32": mixed, "batch": batch,
-                "serving": serving, "bp_cfl_gain": cfl_gain, "paper_meshes": paper_meshes,
+                "serving": serving, "bp_cfl_gain": cfl_gain, "paper_meshes": paper_meshes, "scalar": scalar,
                 "peaks": {"source": peak_src, "hbm_gbs": peaks.get("hbm_gbs")},
                 "stats": {"limited_cells": st["limited_cells"], "cfl_breaches": st["cfl_breaches"],
                           "t": st["t"], "dt_last": st["dt_last"]}}

@@ -25,6 +25,7 @@ recorded by the caller.
 """
 from __future__ import annotations
 
+import functools
 import math
 from dataclasses import dataclass, field
 
@@ -293,6 +294,7 @@ def refine_mesh(mesh: Mesh) -> Mesh:
                 box=mesh.box, meta={**mesh.meta, "refined": mesh.meta.get("refined", 0) + 1})
 
 
+@functools.lru_cache(maxsize=8)
 def scalar_mesh(level: int, n0: int = 5, seed: int = 31) -> Mesh:
     """Periodic unit square: a jittered n0 x n0 grid (2 n0^2 = 50 cells, about
     the paper's 44-cell coarsest mesh) refined ``level`` times."""
