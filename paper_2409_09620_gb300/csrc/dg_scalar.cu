@@ -33,8 +33,14 @@ namespace sc {
 // mode is a sum of terms c xi^p eta^q; d^(r+s)/dxi^r deta^s is taken term by
 // term.  constexpr, so evaluations at fixed points fold to constants.
 // --------------------------------------------------------------------------
-__host__ __device__ constexpr double ipow(double x, int n) { return n <= 0 ? 1.0 : x * ipow(x, n - 1); }
-__host__ __device__ constexpr double fall(int n, int r) { return r <= 0 ? 1.0 : double(n) * fall(n - 1, r - 1); }
+// flat (non-recursive) helpers for exponents and orders up to 3, so that the
+// optimiser folds every evaluation at the fixed points into a constant
+__host__ __device__ constexpr double ipow(double x, int n) {
+  return n <= 0 ? 1.0 : n == 1 ? x : n == 2 ? x * x : x * x * x;
+}
+__host__ __device__ constexpr double fall(int n, int r) {   // n (n-1) ... (n-r+1)
+  return r <= 0 ? 1.0 : r == 1 ? double(n) : r == 2 ? double(n * (n - 1)) : double(n * (n - 1) * (n - 2));
+}
 __host__ __device__ constexpr double term(double c, int p, int q, int r, int s, double x, double y) {
   return (r > p || s > q) ? 0.0 : c * fall(p, r) * fall(q, s) * ipow(x, p - r) * ipow(y, q - s);
 }
