@@ -560,7 +560,7 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         wl_full = make_workload(args.workload, args.nx, args.ny)
-        rate, done, el, threads = oracle_rate(wl_full, steps=3, max_seconds=25.0)
+        rate, done, el, threads = oracle_rate(wl_full, steps=10, max_seconds=25.0)
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"{done} oracle SSP-RK3 step(s) of the full {nt}-cell workload ({el:.1f} s)"}
 
