@@ -45,6 +45,7 @@ struct MeshDev {
   // rounded values, without a conversion per read), and 1/|K| in FP64
   const float *jinv_f, *nrm_f, *len_f, *hgeo_f;
   const double *iarea;
+  const float *node_f;     // [4][nt] FP32 copy of node (P2 internal limiter nodes)
 };
 
 // geometry in the working precision of a kernel
@@ -148,6 +149,16 @@ __host__ __device__ constexpr double psi_x(int l, double x, double y) {   // d/d
 __host__ __device__ constexpr double psi_y(int l, double x, double y) {   // d/deta
   return l == 0 ? 0.0 : l == 1 ? 2.0 : l == 2 ? 3.0 : l == 3 ? 24.0 * x + 8.0 * y - 8.0
        : l == 4 ? 20.0 * x + 20.0 * y - 12.0 : 20.0 * y - 8.0;
+}
+// the same basis evaluated in the arithmetic of T at run-time points
+template <typename T>
+__device__ __forceinline__ T psi_t(int l, T x, T y) {
+  return l == 0 ? T(1)
+       : l == 1 ? T(4) * x + T(2) * y - T(2)
+       : l == 2 ? T(3) * y - T(1)
+       : l == 3 ? T(24) * x * x + T(24) * x * y + T(4) * y * y - T(24) * x - T(8) * y + T(4)
+       : l == 4 ? T(20) * x * y + T(10) * y * y - T(4) * x - T(12) * y + T(2)
+                : T(10) * y * y - T(8) * y + T(1);
 }
 // second reference derivatives: r = 0 (xi xi), 1 (xi eta), 2 (eta eta)
 __host__ __device__ constexpr double psi_2(int l, int r) {

@@ -14,6 +14,7 @@ struct GeomPtrs {
   int8_t *limv;
   float *jinv_f, *nrm_f, *len_f, *hgeo_f;
   double *iarea;
+  float *node_f;
 };
 
 // a modal state: FP64 averages [4][nt] + higher modes [4][nb-1][nt] (double or float)

@@ -21,7 +21,7 @@ __global__ void __launch_bounds__(TPB) k_geometry(int64_t nt, const double *__re
                                                   double *jinv, double *nrm, double *len, double *hgeo,
                                                   double *node, int8_t *limv, double *c_area, double *part_min,
                                                   float *jinv_f, float *nrm_f, float *len_f, float *hgeo_f,
-                                                  double *iarea) {
+                                                  double *iarea, float *node_f) {
   const int64_t K = (int64_t)blockIdx.x * TPB + threadIdx.x;
   double mins[4] = {INFINITY, INFINITY, INFINITY, INFINITY};
   if (K < nt) {
@@ -85,7 +85,10 @@ __global__ void __launch_bounds__(TPB) k_geometry(int64_t nt, const double *__re
     }
     iarea[K] = 1.0 / ar;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) jinv_f[q * nt + K] = float(jinv[q * nt + K]);
+    for (int q = 0; q < 4; ++q) {
+      jinv_f[q * nt + K] = float(jinv[q * nt + K]);
+      node_f[q * nt + K] = float(node[q * nt + K]);
+    }
 #pragma unroll
     for (int q = 0; q < 6; ++q) {
       nrm_f[q * nt + K] = float(nrm[q * nt + K]);
@@ -155,7 +158,7 @@ void launch_geometry(cudaStream_t s, int64_t nt, const double *vxy, const GeomPt
                      double *out_min4) {
   const unsigned nb = nblocks(nt);
   k_geometry<<<nb, TPB, 0, s>>>(nt, vxy, g.area, g.jinv, g.nrm, g.len, g.hgeo, g.node, g.limv, g.c_area, part_min,
-                                g.jinv_f, g.nrm_f, g.len_f, g.hgeo_f, g.iarea);
+                                g.jinv_f, g.nrm_f, g.len_f, g.hgeo_f, g.iarea, g.node_f);
   k_fin_min4<<<1, FIN_THREADS, 0, s>>>(part_min, (int)nb, out_min4);
 }
 

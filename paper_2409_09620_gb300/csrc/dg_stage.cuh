@@ -208,6 +208,8 @@ __device__ __forceinline__ void rk_tile(const MeshDev &m, const Phys &ph, StateD
     Real cu[4][NB];
     load_state<Real, NB>(un, nt, Kc, un0, cu);
     const double dta = dt * m.iarea[Kc];
+    // the stage coefficients in the working precision, converted once
+    const Real ar = Real(a), br = Real(b), dtar = Real(dta);
     double h0[4];
     Real hh[4][NB];
     Real h0r[4];
@@ -221,8 +223,8 @@ __device__ __forceinline__ void rk_tile(const MeshDev &m, const Phys &ph, StateD
       hh[c][0] = Real(0);
 #pragma unroll
       for (int l = 1; l < NB; ++l) {
-        const Real s = sizeof(Real) == sizeof(double) ? Real(dta * inv_mass_c(l)) : Real(dta) * Real(inv_mass_c(l));
-        hh[c][l] = Real(a) * cu[c][l] + Real(b) * (cv[c][l] + s * acc[c][l]);
+        const Real s = sizeof(Real) == sizeof(double) ? Real(dta * inv_mass_c(l)) : dtar * Real(inv_mass_c(l));
+        hh[c][l] = ar * cu[c][l] + br * (cv[c][l] + s * acc[c][l]);
         uh.hi[(c * (NB - 1) + (l - 1)) * nt + Kc] = hh[c][l];
       }
     }
@@ -516,8 +518,7 @@ __device__ __forceinline__ void edge_tile(const MeshDev &m, const Phys &ph, cons
 // fell back to its average.
 template <int K>
 __device__ __noinline__ void limit_mixed_fp64(const MeshDev &m, const Phys &ph, const double *a0p, const float *hip,
-                                              const double *pxp, const double *pyp, StateDev<float> out, int64_t Kc,
-                                              float *utp, long long *limited) {
+                                              StateDev<float> out, int64_t Kc, float *utp, long long *limited) {
   constexpr int NB = Deg<K>::NB, NQ = Deg<K>::NQ, NE = 3 * NQ;
   const int64_t nt = m.nt;
   double a0[4], px[2], py[2];
@@ -528,7 +529,13 @@ __device__ __noinline__ void limit_mixed_fp64(const MeshDev &m, const Phys &ph, 
 #pragma unroll
     for (int l = 0; l < NB; ++l) hi[c][l] = hip[c * NB + l];
   }
-  px[0] = pxp[0]; px[1] = pxp[1]; py[0] = pyp[0]; py[1] = pyp[1];
+  // the two extra points of the limiter set in FP64 (P1: vertices v1, v2; P2: internal nodes)
+  if (K == 1) {
+    const int v1 = m.limv[Kc], v2 = m.limv[nt + Kc];
+    px[0] = vert_xi(v1); py[0] = vert_eta(v1); px[1] = vert_xi(v2); py[1] = vert_eta(v2);
+  } else {
+    px[0] = m.node[Kc]; py[0] = m.node[nt + Kc]; px[1] = m.node[2 * nt + Kc]; py[1] = m.node[3 * nt + Kc];
+  }
   float ut[NE][4];
   long long cnt[1] = {0};
     // ---- FP64 theta (Sec. 4.4 Steps 1-2) with targets covering the FP32 store
@@ -673,13 +680,14 @@ __device__ __forceinline__ void limit_and_trace_mixed(const MeshDev &m, const Ph
   constexpr int NB = Deg<K>::NB, NQ = Deg<K>::NQ, NE = 3 * NQ;
   const int64_t nt = m.nt;
   const float gamma = float(ph.gamma), gm1 = float(ph.gamma - 1.0);
-  // the two extra points of the limiter set (P1: vertices v1, v2; P2: internal nodes)
-  double px[2], py[2];
+  // the two extra points of the limiter set for the FP32 screen (P1: vertices
+  // v1, v2; P2: internal nodes, from the mesh's FP32 copy)
+  float px[2], py[2];
   if (K == 1) {
     const int v1 = m.limv[Kc], v2 = m.limv[nt + Kc];
-    px[0] = vert_xi(v1); py[0] = vert_eta(v1); px[1] = vert_xi(v2); py[1] = vert_eta(v2);
+    px[0] = float(vert_xi(v1)); py[0] = float(vert_eta(v1)); px[1] = float(vert_xi(v2)); py[1] = float(vert_eta(v2));
   } else {
-    px[0] = m.node[Kc]; py[0] = m.node[nt + Kc]; px[1] = m.node[2 * nt + Kc]; py[1] = m.node[3 * nt + Kc];
+    px[0] = m.node_f[Kc]; py[0] = m.node_f[nt + Kc]; px[1] = m.node_f[2 * nt + Kc]; py[1] = m.node_f[3 * nt + Kc];
   }
   // FP32 deviations u - ubar at the edge Gauss points
   float df[NE][4];
@@ -745,7 +753,7 @@ __device__ __forceinline__ void limit_and_trace_mixed(const MeshDev &m, const Ph
           for (int c = 0; c < 4; ++c) {
             float sacc = 0.0f;
 #pragma unroll
-            for (int l = 1; l < NB; ++l) sacc = fmaf(float(psi(l, px[p], py[p])), hi[c][l], sacc);
+            for (int l = 1; l < NB; ++l) sacc = fmaf(psi_t<float>(l, px[p], py[p]), hi[c][l], sacc);
             dx[NE + p][c] = sacc;
           }
       }
@@ -766,7 +774,7 @@ __device__ __forceinline__ void limit_and_trace_mixed(const MeshDev &m, const Ph
       for (int c = 0; c < 4; ++c) ut[p][c] = a0f[c] + df[p][c];
   } else {
     // FP64 theta (Sec. 4.4 Steps 1-2) out of line
-    double a0l[4], pxl[2] = {px[0], px[1]}, pyl[2] = {py[0], py[1]};
+    double a0l[4];
     float hl[4][NB], utl[NE][4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
@@ -775,7 +783,7 @@ __device__ __forceinline__ void limit_and_trace_mixed(const MeshDev &m, const Ph
       for (int l = 0; l < NB; ++l) hl[c][l] = hi[c][l];
     }
     long long lim = 0;
-    limit_mixed_fp64<K>(m, ph, a0l, &hl[0][0], pxl, pyl, out, Kc, &utl[0][0], &lim);
+    limit_mixed_fp64<K>(m, ph, a0l, &hl[0][0], out, Kc, &utl[0][0], &lim);
     if (lim) cnt[0] = 1;
 #pragma unroll
     for (int p = 0; p < NE; ++p)
