@@ -244,6 +244,11 @@ __device__ __forceinline__ void flux_dir2(const T u[4], T d1x, T d1y, T d2x, T d
   f2[0] = m2; f2[1] = fma(u[1], v2, p * d2x); f2[2] = fma(u[2], v2, p * d2y); f2[3] = ep * v2;
 }
 
+// x > 0 on the integer units for doubles (differs from the comparison only
+// for a NaN with a clear sign bit); a plain comparison for floats
+__device__ __forceinline__ bool gt0(double x) { return __double_as_longlong(x) > 0; }
+__device__ __forceinline__ bool gt0(float x) { return x > 0.0f; }
+
 // F(u) . n and the spectral radius |v.n| + c (+inf for rho <= 0) with one reciprocal
 template <typename T>
 __device__ __forceinline__ T flux_speed(const T u[4], T nx, T ny, T gm1, T gamma, T f[4]) {
@@ -255,18 +260,18 @@ __device__ __forceinline__ T flux_speed(const T u[4], T nx, T ny, T gm1, T gamma
   f[1] = fma(u[1], vn, p * nx);
   f[2] = fma(u[2], vn, p * ny);
   f[3] = (u[3] + p) * vn;
-  if (!(u[0] > T(0))) return T(INFINITY);
-  const T pc = p > T(0) ? p : T(0);
+  if (!gt0(u[0])) return T(INFINITY);
+  const T pc = gt0(p) ? p : T(0);
   return fabs(vn) + sqrt(gamma * pc * ri);
 }
 
 // spectral radius |v.n| + c; +inf for rho <= 0, pressure clamped at 0
 template <typename T>
 __device__ __forceinline__ T wave_speed(const T u[4], T nx, T ny, T gamma) {
-  if (!(u[0] > T(0))) return T(INFINITY);
+  if (!gt0(u[0])) return T(INFINITY);
   const T ri = T(1) / u[0];
   T p = (gamma - T(1)) * (u[3] - T(0.5) * (u[1] * u[1] + u[2] * u[2]) * ri);
-  p = p > T(0) ? p : T(0);
+  p = gt0(p) ? p : T(0);
   return fabs(u[1] * nx + u[2] * ny) * ri + sqrt(gamma * p * ri);
 }
 

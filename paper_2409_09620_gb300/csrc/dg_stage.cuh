@@ -317,11 +317,13 @@ __device__ __forceinline__ void stats_tile(const MeshDev &m, StateDev<Real> uh, 
       Real u[4];
       eval_fixed<Real, NB>(off, hi, vol_xi(NV, mu), vol_eta(NV, mu), u);
       dr[0] = max_nn(dr[0], fabs(u[0]));
-      dr[1] = max_nn(dr[1], sqrt(u[1] * u[1] + u[2] * u[2]));
+      dr[1] = max_nn(dr[1], u[1] * u[1] + u[2] * u[2]);   // squared: one square root per cell below
       dr[2] = max_nn(dr[2], fabs(u[3]));
       dr[3] = max_nn(dr[3], fabs(u[1]));
       dr[4] = max_nn(dr[4], fabs(u[2]));
     }
+    // sqrt is monotonic and correctly rounded: sqrt(max) = max(sqrt), bit for bit
+    dr[1] = sqrt(dr[1]);
   }
   block_reduce<5>(dr, part_dev + 5 * tile, OpMaxNN());
 }
