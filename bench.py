@@ -357,7 +357,7 @@ def main():
         except Exception as exc:      # mixed precision not available
             mixed = {"error": str(exc)}
 
-    # batch of 64 independent solves, one persistent launch per RK stage
+    # batch of 64 independent solves over one work list, launch form and shape autotuned
     batch = None
     if not args.no_batch:
         from paper_2409_09620_gb300 import workloads as W

@@ -194,26 +194,27 @@ int32_t dg_op_limit(dg_solver *solver, const double *u, double *out, int64_t *co
 int32_t dg_op_alpha(dg_solver *solver, const double *u, double t, double *alpha);
 
 /* ---------------------------------------------------------------------- */
-/* Batches: many independent solves, one persistent launch per RK stage     */
+/* Batches: many independent solves advanced together                      */
 /* ---------------------------------------------------------------------- */
 
 /* Create a batch of n independent solves (meshes[i], cfgs[i], host initial
  * coefficients coeffs[i]; k may differ between solves, the precision may not).
  * Each solve is set up as by dg_init on the batch's stream (NULL = a stream
- * the batch creates).  A time step of all solves is three cooperative
- * launches of one persistent kernel (one per SSP-RK3 stage, captured as a CUDA
- * graph when the runtime supports it); each launch walks a work list of
- * (solve, cell range) chunks with grid barriers between the phases of the
- * stage.  Every solve keeps its own alpha, dt, t and OE normalisers, and its
- * results are bitwise those of the same solve run alone.  Errors as dg_init;
- * DG_EINVAL if the precisions differ or the device lacks cooperative launch. */
+ * the batch creates).  A stage of all solves walks a work list of (solve,
+ * cell range) chunks in three phases (flux; OE statistics; OE + limiter),
+ * in one of two launch forms: 3 = one ordinary launch per phase (default),
+ * 1 = one persistent cooperative launch per stage with grid barriers between
+ * the phases.  A step is captured as a CUDA graph when the runtime supports
+ * it.  Every solve keeps its own alpha, dt, t and OE normalisers, and its
+ * results are bitwise those of the same solve run alone, in either form.
+ * Errors as dg_init; DG_EINVAL if the precisions differ. */
 int32_t dg_batch_create(int32_t n, const dg_mesh *const *meshes, const dg_config *cfgs,
                         const double *const *coeffs, void *cuda_stream, dg_batch **out);
 void dg_batch_destroy(dg_batch *batch);
 /* Advance every solve i until t_i >= t_end[i] (t_end NULL: +inf) or max_steps
  * steps; solves that reached their end time idle.  stats (nullable) receives n
- * entries.  A grid barrier that waits longer than 2 s ends the launch early
- * and the call returns DG_ETIMEOUT. */
+ * entries.  In form 1, a grid barrier that waits longer than 2 s ends the
+ * launch early and the call returns DG_ETIMEOUT. */
 int32_t dg_batch_advance(dg_batch *batch, const double *t_end, int64_t max_steps, dg_stats *stats);
 /* enqueue exactly n steps of every solve; pair with dg_batch_sync */
 int32_t dg_batch_advance_async(dg_batch *batch, int64_t nsteps);
@@ -221,17 +222,22 @@ int32_t dg_batch_sync(dg_batch *batch);
 /* the solver handle of solve i (owned by the batch): dg_get_state /
  * dg_set_state work on it; do not destroy it or advance it on its own */
 int32_t dg_batch_solver(dg_batch *batch, int32_t i, dg_solver **out);
-/* launch shape: cells per work chunk (a positive multiple of 128) and resident
- * blocks per SM of the persistent grid (clamped to the occupancy limit) */
-int32_t dg_batch_set_shape(dg_batch *batch, int32_t cells_per_block, int32_t blocks_per_sm);
+/* launch shape: cells per work chunk (a positive multiple of 128), resident
+ * blocks per SM of each launch's grid (clamped per kernel to its occupancy
+ * limit) and the launch form (launches per stage: 3 or 1).  DG_EINVAL for
+ * another form, or form 1 on a device without cooperative launch.  *grid
+ * receives the largest grid of the form's launches. */
+int32_t dg_batch_set_shape(dg_batch *batch, int32_t cells_per_block, int32_t blocks_per_sm,
+                           int32_t launches_per_stage);
 int32_t dg_batch_shape(const dg_batch *batch, int32_t *cells_per_block, int32_t *blocks_per_sm,
-                       int32_t *grid, int32_t *graph);
-/* Time `steps` steps for every cells-per-chunk in {128, 256, 512, 1024} and
- * every blocks-per-SM up to the occupancy limit, keep the fastest shape and
- * restore every solve's state, time and counters.  The shape changes no
- * result (partials are per 128 cells of each solve). */
+                       int32_t *launches_per_stage, int32_t *grid, int32_t *graph);
+/* Time `steps` steps for both launch forms, every cells-per-chunk in {128,
+ * 256, 512, 1024} and every blocks-per-SM up to the occupancy limit, keep the
+ * fastest shape and restore every solve's state, time and counters.  The
+ * shape changes no result (partials are per 128 cells of each solve). */
 int32_t dg_batch_autotune(dg_batch *batch, int32_t steps, int32_t *best_cells_per_block,
-                          int32_t *best_blocks_per_sm, double *best_ms_per_step);
+                          int32_t *best_blocks_per_sm, int32_t *best_launches_per_stage,
+                          double *best_ms_per_step);
 
 /* ---------------------------------------------------------------------- */
 /* Serving: continuous batching of independent solve requests               */

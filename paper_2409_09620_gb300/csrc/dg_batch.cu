@@ -1,16 +1,17 @@
-// dg_batch.cu -- many independent solves advanced together: one persistent
-// (cooperative) launch per SSP-RK3 stage covers every solve.  Each launch runs
-// the three phases of a stage (flux + means; deviations, edge records and OE
-// normalisers; RIOE + limiter + alpha) over a work list of (solve, tile range)
-// chunks, separated by grid barriers.  Each phase finalises its reductions in
-// the block that completes them, in the same fixed order as the per-solve
-// kernels.
+// dg_batch.cu -- many independent solves advanced together over a work list
+// of (solve, tile range) chunks.  A stage has three phases (flux + means;
+// deviations, edge records and OE normalisers; RIOE + limiter + alpha).  They
+// run either as one persistent cooperative launch per stage with grid
+// barriers between the phases, or as one ordinary launch per phase, each at
+// the occupancy of the per-solve kernel of that phase; the autotuner picks.
+// Each phase finalises its reductions in the block that completes them, in
+// the same fixed order as the per-solve kernels.
 //
 // Every solve keeps its own buffers, scalars (t, dt, alpha, normalisers) and
 // per-tile partials; tiles never straddle solves and partials are per TPB
 // cells from each solve's first cell, so a solve's arithmetic does not depend
-// on the other solves or on the chunk size: results are bitwise those of the
-// same solve run alone.
+// on the other solves, the chunk size or the launch form: results are bitwise
+// those of the same solve run alone.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -92,20 +93,15 @@ __device__ __forceinline__ bool grid_sync(BarrierState *b, unsigned nblocks) {
   return s_ok;
 }
 
+// The three phases of a stage over the work list, blocks [first, first +
+// stride, ...).  Each tile finalises its reductions through the tickets, so
+// the phases need only be ordered, by a grid barrier or a kernel boundary.
 template <typename Real>
-__global__ void __launch_bounds__(TPB) k_batch_stage(const SolveDev *__restrict__ sv, int nsv,
-                                                     const WorkItem *__restrict__ work, int nwork,
-                                                     BarrierState *bar, int stage) {
-  const unsigned nb = gridDim.x;
-  const double a = kRK_A[stage], b = kRK_B[stage], c_in = kC_IN[stage], c_out = kC_OUT[stage];
+__device__ __forceinline__ void phase_rk(const SolveDev *__restrict__ sv, const WorkItem *__restrict__ work,
+                                         int nwork, int stage) {
+  const double a = kRK_A[stage], b = kRK_B[stage], c_in = kC_IN[stage];
   const int vi = stage == 0 ? 0 : 2;     // stage input: u_n, then u_s
-  const int oi = stage == 2 ? 0 : 2;     // stage output: u_s, last stage writes u_n
-  if (stage == 0) {
-    if (threadIdx.x == 0)
-      for (int i = blockIdx.x; i < nsv; i += gridDim.x) step_begin_thread(sv[i].sc);
-    if (!grid_sync(bar, nb)) return;
-  }
-  // phase 1: volume + edge fluxes + RK combination; domain means
+  // volume + edge fluxes + RK combination; domain means
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
     const WorkItem it = work[w];
     const SolveDev &S = sv[it.solve];
@@ -121,8 +117,13 @@ __global__ void __launch_bounds__(TPB) k_batch_stage(const SolveDev *__restrict_
       finish_means(S.part_sum, S.fin, t, S.ntiles, S.sc);
     }
   }
-  if (!grid_sync(bar, nb)) return;
-  // phase 2: sup deviations at the volume points, edge OE records; normalisers
+}
+
+template <typename Real>
+__device__ __forceinline__ void phase_stats(const SolveDev *__restrict__ sv, const WorkItem *__restrict__ work,
+                                            int nwork, int stage) {
+  const double c_out = kC_OUT[stage];
+  // sup deviations at the volume points, edge OE records; normalisers
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
     const WorkItem it = work[w];
     const SolveDev &S = sv[it.solve];
@@ -139,8 +140,14 @@ __global__ void __launch_bounds__(TPB) k_batch_stage(const SolveDev *__restrict_
       finish_deviations(S.part_dev, S.fin, t, S.ntiles, S.sc, S.oe == 2);
     }
   }
-  if (!grid_sync(bar, nb)) return;
-  // phase 3: RIOE + BP limiter + traces; alpha of the stage result, time update
+}
+
+template <typename Real>
+__device__ __forceinline__ void phase_oe_bp(const SolveDev *__restrict__ sv, const WorkItem *__restrict__ work,
+                                            int nwork, int stage) {
+  const double c_out = kC_OUT[stage];
+  const int oi = stage == 2 ? 0 : 2;     // stage output: u_s, last stage writes u_n
+  // RIOE + BP limiter + traces; alpha of the stage result, time update
   for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
     const WorkItem it = work[w];
     const SolveDev &S = sv[it.solve];
@@ -158,13 +165,60 @@ __global__ void __launch_bounds__(TPB) k_batch_stage(const SolveDev *__restrict_
   }
 }
 
+// Fused form: one cooperative launch per stage runs the three phases with
+// grid barriers between them (and the step start before stage 0).
+template <typename Real>
+__global__ void __launch_bounds__(TPB) k_batch_stage(const SolveDev *__restrict__ sv, int nsv,
+                                                     const WorkItem *__restrict__ work, int nwork,
+                                                     BarrierState *bar, int stage) {
+  const unsigned nb = gridDim.x;
+  if (stage == 0) {
+    if (threadIdx.x == 0)
+      for (int i = blockIdx.x; i < nsv; i += gridDim.x) step_begin_thread(sv[i].sc);
+    if (!grid_sync(bar, nb)) return;
+  }
+  phase_rk<Real>(sv, work, nwork, stage);
+  if (!grid_sync(bar, nb)) return;
+  phase_stats<Real>(sv, work, nwork, stage);
+  if (!grid_sync(bar, nb)) return;
+  phase_oe_bp<Real>(sv, work, nwork, stage);
+}
+
+// Phased form: one ordinary launch per phase, each with the register budget
+// and occupancy of the per-solve kernel of that phase; kernel boundaries
+// order the phases, so no block ever waits on another.
+__global__ void __launch_bounds__(TPB) k_batch_begin(const SolveDev *__restrict__ sv, int nsv) {
+  const int i = blockIdx.x * TPB + threadIdx.x;
+  if (i < nsv) step_begin_thread(sv[i].sc);
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(TPB, sizeof(Real) == 4 ? RK_MINB_F : RK_MINB_D)
+    k_batch_rk(const SolveDev *__restrict__ sv, const WorkItem *__restrict__ work, int nwork, int stage) {
+  phase_rk<Real>(sv, work, nwork, stage);
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(TPB, sizeof(Real) == 4 ? STATS_MINB_F : STATS_MINB_D)
+    k_batch_stats(const SolveDev *__restrict__ sv, const WorkItem *__restrict__ work, int nwork, int stage) {
+  phase_stats<Real>(sv, work, nwork, stage);
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(TPB, sizeof(Real) == 4 ? OEBP_MINB_F : OEBP_MINB_D)
+    k_batch_oe_bp(const SolveDev *__restrict__ sv, const WorkItem *__restrict__ work, int nwork, int stage) {
+  phase_oe_bp<Real>(sv, work, nwork, stage);
+}
+
 }  // namespace dg
 
 using namespace dg;
 
 namespace dg {
 
-// A set of solves advanced together by the persistent stage kernel.  The set
+// A set of solves advanced together.  A step is either three cooperative
+// launches of the fused stage kernel (form 1) or, per stage, three ordinary
+// launches of the phase kernels after one step-start launch (form 3).  The set
 // can change between steps (set_solves): the solve descriptors, the work list
 // and the step graph are rebuilt.
 struct BatchCore {
@@ -177,7 +231,8 @@ struct BatchCore {
   WorkItem *d_work = nullptr;
   size_t work_cap = 0;
   BarrierState *d_bar = nullptr;
-  int nwork = 0, grid = 0, cpb = 4 * TPB, max_blocks_per_sm = 0, blocks_per_sm = 0, num_sms = 0;
+  int nwork = 0, grid = 0, cpb = 4 * TPB, blocks_per_sm = 0, num_sms = 0, form = 3;
+  int occ_fused = 0, occ_phase[3] = {0, 0, 0}, grid_phase[3] = {0, 0, 0};
   cudaGraphExec_t exec = nullptr;
   bool graph_ok = false;
 
@@ -196,25 +251,63 @@ struct BatchCore {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-    if (!coop) return set_error(DG_EINVAL, "device does not support cooperative launches");
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&max_blocks_per_sm, kernel(), TPB, 0) != cudaSuccess ||
-        max_blocks_per_sm < 1)
+    if (coop && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_fused, fused_kernel(), TPB, 0) != cudaSuccess))
       return set_error(DG_ECUDA, "occupancy query failed");
-    blocks_per_sm = max_blocks_per_sm;
+    if (!coop) occ_fused = 0;
+    for (int p = 0; p < 3; ++p)
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_phase[p], phase_kernel(p), TPB, 0) != cudaSuccess ||
+          occ_phase[p] < 1)
+        return set_error(DG_ECUDA, "occupancy query failed");
+    form = 3;
+    blocks_per_sm = max_blocks_per_sm(form);
     if (cudaMalloc(&d_bar, sizeof(BarrierState)) != cudaSuccess) return set_error(DG_ENOMEM, "barrier state");
     BarrierState z{};
     if (cudaMemcpy(d_bar, &z, sizeof(z), cudaMemcpyHostToDevice) != cudaSuccess) return set_error(DG_ECUDA, "barrier");
     return DG_OK;
   }
 
-  const void *kernel() const {
+  // resident blocks per SM of the form's kernels (0: form unavailable)
+  int max_blocks_per_sm(int f) const {
+    return f == 1 ? occ_fused : std::max(occ_phase[0], std::max(occ_phase[1], occ_phase[2]));
+  }
+
+  const void *fused_kernel() const {
     return prec == DG_PREC_MIXED ? (const void *)k_batch_stage<float> : (const void *)k_batch_stage<double>;
+  }
+
+  const void *phase_kernel(int p) const {
+    if (prec == DG_PREC_MIXED)
+      return p == 0 ? (const void *)k_batch_rk<float> : p == 1 ? (const void *)k_batch_stats<float>
+                                                               : (const void *)k_batch_oe_bp<float>;
+    return p == 0 ? (const void *)k_batch_rk<double> : p == 1 ? (const void *)k_batch_stats<double>
+                                                              : (const void *)k_batch_oe_bp<double>;
+  }
+
+  size_t stack_bytes() const {
+    if (prec == DG_PREC_MIXED)
+      return form == 1 ? kernel_local_bytes(k_batch_stage<float>)
+                       : std::max(kernel_local_bytes(k_batch_rk<float>),
+                                  std::max(kernel_local_bytes(k_batch_stats<float>),
+                                           kernel_local_bytes(k_batch_oe_bp<float>)));
+    return form == 1 ? kernel_local_bytes(k_batch_stage<double>)
+                     : std::max(kernel_local_bytes(k_batch_rk<double>),
+                                std::max(kernel_local_bytes(k_batch_stats<double>),
+                                         kernel_local_bytes(k_batch_oe_bp<double>)));
   }
 
   cudaError_t launch_stage(int stage) {
     int nsv = (int)host_sv.size(), nw = nwork;
-    void *args[] = {&d_sv, &nsv, &d_work, &nw, &d_bar, &stage};
-    return cudaLaunchCooperativeKernel(kernel(), dim3(grid), dim3(TPB), args, 0, stream);
+    if (form == 1) {
+      void *args[] = {&d_sv, &nsv, &d_work, &nw, &d_bar, &stage};
+      return cudaLaunchCooperativeKernel(fused_kernel(), dim3(grid), dim3(TPB), args, 0, stream);
+    }
+    if (stage == 0) k_batch_begin<<<(nsv + TPB - 1) / TPB, TPB, 0, stream>>>(d_sv, nsv);
+    void *args[] = {&d_sv, &d_work, &nw, &stage};
+    for (int p = 0; p < 3; ++p) {
+      cudaError_t e = cudaLaunchKernel(phase_kernel(p), dim3(grid_phase[p]), dim3(TPB), args, 0, stream);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
   }
 
   // the solves to advance (not owned); rebuilds descriptors, work list and graph
@@ -251,11 +344,14 @@ struct BatchCore {
     if (!host_sv.empty() &&
         cudaMemcpy(d_sv, host_sv.data(), sizeof(SolveDev) * host_sv.size(), cudaMemcpyHostToDevice) != cudaSuccess)
       return set_error(DG_ECUDA, "solve table upload");
-    return set_shape(cpb, blocks_per_sm);
+    return set_shape(cpb, blocks_per_sm, form);
   }
 
   // work list of chunks of cpb cells (a multiple of TPB), then the step graph
-  int32_t set_shape(int cells_per_block, int bpsm) {
+  int32_t set_shape(int cells_per_block, int bpsm, int launch_form) {
+    if (launch_form != 1 && launch_form != 3) return set_error(DG_EINVAL, "launches per stage must be 1 or 3");
+    if (max_blocks_per_sm(launch_form) < 1)
+      return set_error(DG_EINVAL, "the device does not support cooperative launches");
     std::vector<WorkItem> work;
     const int64_t tpw = cells_per_block / TPB;
     for (size_t i = 0; i < host_sv.size(); ++i)
@@ -272,15 +368,23 @@ struct BatchCore {
       return set_error(DG_ECUDA, "work list upload");
     nwork = (int)work.size();
     cpb = cells_per_block;
-    blocks_per_sm = std::max(1, std::min(bpsm, max_blocks_per_sm));
-    grid = std::max(1, std::min(num_sms * blocks_per_sm, std::max(nwork, 1)));
-    // one SSP-RK3 step = three cooperative launches, captured as a graph when supported
+    form = launch_form;
+    blocks_per_sm = std::max(1, std::min(bpsm, max_blocks_per_sm(form)));
+    const int nw = std::max(nwork, 1);
+    if (form == 1) {
+      grid = std::max(1, std::min(num_sms * blocks_per_sm, nw));
+    } else {
+      grid = 0;
+      for (int p = 0; p < 3; ++p) {
+        grid_phase[p] = std::max(1, std::min(num_sms * std::min(blocks_per_sm, occ_phase[p]), nw));
+        grid = std::max(grid, grid_phase[p]);
+      }
+    }
+    // one SSP-RK3 step, captured as a graph when supported
     if (exec) { cudaGraphExecDestroy(exec); exec = nullptr; }
     graph_ok = false;
     if (host_sv.empty()) return DG_OK;
-    const size_t stack = prec == DG_PREC_MIXED ? kernel_local_bytes(k_batch_stage<float>)
-                                               : kernel_local_bytes(k_batch_stage<double>);
-    int32_t rc = ensure_stack_limit(stack);
+    int32_t rc = ensure_stack_limit(stack_bytes());
     if (rc != DG_OK) return rc;
     cudaGraph_t g = nullptr;
     if (cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
@@ -375,18 +479,20 @@ extern "C" int32_t dg_batch_create(int32_t n, const dg_mesh *const *meshes, cons
 
 extern "C" void dg_batch_destroy(dg_batch *b) { delete b; }
 
-extern "C" int32_t dg_batch_set_shape(dg_batch *b, int32_t cells_per_block, int32_t blocks_per_sm) {
+extern "C" int32_t dg_batch_set_shape(dg_batch *b, int32_t cells_per_block, int32_t blocks_per_sm,
+                                      int32_t launches_per_stage) {
   if (!b || cells_per_block < TPB || cells_per_block % TPB != 0 || blocks_per_sm < 1)
     return set_error(DG_EINVAL, "cells_per_block must be a positive multiple of 128, blocks_per_sm >= 1");
   if (cudaStreamSynchronize(b->stream) != cudaSuccess) return set_error(DG_ECUDA, "sync");
-  return b->core.set_shape(cells_per_block, blocks_per_sm);
+  return b->core.set_shape(cells_per_block, blocks_per_sm, launches_per_stage);
 }
 
 extern "C" int32_t dg_batch_shape(const dg_batch *b, int32_t *cells_per_block, int32_t *blocks_per_sm,
-                                  int32_t *grid, int32_t *graph) {
+                                  int32_t *launches_per_stage, int32_t *grid, int32_t *graph) {
   if (!b) return set_error(DG_EINVAL, "batch is NULL");
   if (cells_per_block) *cells_per_block = b->core.cpb;
   if (blocks_per_sm) *blocks_per_sm = b->core.blocks_per_sm;
+  if (launches_per_stage) *launches_per_stage = b->core.form;
   if (grid) *grid = b->core.grid;
   if (graph) *graph = b->core.graph_ok ? 1 : 0;
   return DG_OK;
@@ -465,7 +571,7 @@ extern "C" int32_t dg_batch_solver(dg_batch *b, int32_t i, dg_solver **out) {
 }
 
 extern "C" int32_t dg_batch_autotune(dg_batch *b, int32_t steps, int32_t *best_cpb, int32_t *best_bpsm,
-                                     double *best_ms) {
+                                     int32_t *best_launches, double *best_ms) {
   if (!b || steps < 1) return set_error(DG_EINVAL, "bad argument");
   BatchCore &core = b->core;
   const int n = (int)core.solves.size();
@@ -497,21 +603,23 @@ extern "C" int32_t dg_batch_autotune(dg_batch *b, int32_t steps, int32_t *best_c
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   double best = INFINITY;
-  int bc = core.cpb, bb = core.blocks_per_sm;
+  int bc = core.cpb, bb = core.blocks_per_sm, bf = core.form;
   const int cpbs[4] = {TPB, 2 * TPB, 4 * TPB, 8 * TPB};
-  for (int ci = 0; ci < 4; ++ci)
-    for (int bpsm = 1; bpsm <= core.max_blocks_per_sm; ++bpsm) {
-      int32_t rc = core.set_shape(cpbs[ci], bpsm);
-      if (rc == DG_OK) rc = core.enqueue_steps(1);   // warm-up
-      cudaEventRecord(e0, core.stream);
-      if (rc == DG_OK) rc = core.enqueue_steps(steps);
-      cudaEventRecord(e1, core.stream);
-      if (rc == DG_OK) rc = core.check_barrier();
-      if (rc != DG_OK) { free_snaps(); return rc; }
-      float ms = 0.0f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (ms < best) { best = ms; bc = cpbs[ci]; bb = bpsm; }
-    }
+  const int forms[2] = {3, 1};
+  for (int fi = 0; fi < 2; ++fi)
+    for (int ci = 0; ci < 4; ++ci)
+      for (int bpsm = 1; bpsm <= core.max_blocks_per_sm(forms[fi]); ++bpsm) {
+        int32_t rc = core.set_shape(cpbs[ci], bpsm, forms[fi]);
+        if (rc == DG_OK) rc = core.enqueue_steps(1);   // warm-up
+        cudaEventRecord(e0, core.stream);
+        if (rc == DG_OK) rc = core.enqueue_steps(steps);
+        cudaEventRecord(e1, core.stream);
+        if (rc == DG_OK) rc = core.check_barrier();
+        if (rc != DG_OK) { free_snaps(); return rc; }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; bc = cpbs[ci]; bb = bpsm; bf = forms[fi]; }
+      }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   for (int i = 0; i < n; ++i) {
@@ -525,10 +633,11 @@ extern "C" int32_t dg_batch_autotune(dg_batch *b, int32_t steps, int32_t *best_c
     if (solver_write_scalars(s, &q.sc) != DG_OK) { free_snaps(); return DG_ECUDA; }
   }
   free_snaps();
-  int32_t rc = core.set_shape(bc, bb);
+  int32_t rc = core.set_shape(bc, bb, bf);
   if (rc != DG_OK) return rc;
   if (best_cpb) *best_cpb = bc;
   if (best_bpsm) *best_bpsm = bb;
+  if (best_launches) *best_launches = bf;
   if (best_ms) *best_ms = best / steps;
   return DG_OK;
 }

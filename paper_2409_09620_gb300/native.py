@@ -90,9 +90,9 @@ SIGNATURES = {
     "dg_batch_advance_async": (i32, [P, i64]),
     "dg_batch_sync": (i32, [P]),
     "dg_batch_solver": (i32, [P, i32, C.POINTER(P)]),
-    "dg_batch_set_shape": (i32, [P, i32, i32]),
-    "dg_batch_shape": (i32, [P, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
-    "dg_batch_autotune": (i32, [P, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(dbl)]),
+    "dg_batch_set_shape": (i32, [P, i32, i32, i32]),
+    "dg_batch_shape": (i32, [P, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
+    "dg_batch_autotune": (i32, [P, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(dbl)]),
     "dg_server_create": (i32, [i32, C.c_size_t, i32, P, C.POINTER(P)]),
     "dg_server_destroy": (None, [P]),
     "dg_server_submit": (i32, [P, i64, P, i64, P, P, P, P, P, dbl, C.POINTER(i64)]),
@@ -332,7 +332,8 @@ class _SolverView(Solver):
 
 
 class Batch:
-    """dg_batch handle: independent solves advanced by one persistent launch per stage."""
+    """dg_batch handle: independent solves advanced together over one work list,
+    one launch per phase (form 3) or one cooperative launch per stage (form 1)."""
 
     def __init__(self, meshes, cfgs, coeffs, stream=None):
         n = len(meshes)
@@ -375,18 +376,20 @@ class Batch:
     def sync(self):
         _check(lib().dg_batch_sync(self.h))
 
-    def set_shape(self, cells_per_block, blocks_per_sm):
-        _check(lib().dg_batch_set_shape(self.h, cells_per_block, blocks_per_sm))
+    def set_shape(self, cells_per_block, blocks_per_sm, launches_per_stage=3):
+        _check(lib().dg_batch_set_shape(self.h, cells_per_block, blocks_per_sm, launches_per_stage))
 
     def shape(self):
-        a, b, g, gr = i32(), i32(), i32(), i32()
-        _check(lib().dg_batch_shape(self.h, C.byref(a), C.byref(b), C.byref(g), C.byref(gr)))
-        return dict(cells_per_block=a.value, blocks_per_sm=b.value, grid=g.value, graph=bool(gr.value))
+        a, b, f, g, gr = i32(), i32(), i32(), i32(), i32()
+        _check(lib().dg_batch_shape(self.h, C.byref(a), C.byref(b), C.byref(f), C.byref(g), C.byref(gr)))
+        return dict(cells_per_block=a.value, blocks_per_sm=b.value, launches_per_stage=f.value, grid=g.value,
+                    graph=bool(gr.value))
 
     def autotune(self, steps=3):
-        a, b, ms = i32(), i32(), dbl()
-        _check(lib().dg_batch_autotune(self.h, steps, C.byref(a), C.byref(b), C.byref(ms)))
-        return dict(cells_per_block=a.value, blocks_per_sm=b.value, ms_per_step=ms.value)
+        a, b, f, ms = i32(), i32(), i32(), dbl()
+        _check(lib().dg_batch_autotune(self.h, steps, C.byref(a), C.byref(b), C.byref(f), C.byref(ms)))
+        return dict(cells_per_block=a.value, blocks_per_sm=b.value, launches_per_stage=f.value,
+                    ms_per_step=ms.value)
 
 
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
