@@ -524,6 +524,8 @@ extern "C" int32_t dg_init(const dg_mesh *mesh, const dg_config *cfg, const doub
   Phys &ph = c.phys;
   std::memset(&ph, 0, sizeof(ph));
   ph.gamma = cfg->gamma;
+  ph.gamma_f = float(cfg->gamma);
+  ph.gm1_f = float(cfg->gamma - 1.0);
   for (int i = 0; i < 4; ++i)
     for (int j = 0; j < 4; ++j) ph.bc[i][j] = cfg->bc_state[i][j];
   ph.shock_x0 = cfg->shock_x0;

@@ -118,13 +118,25 @@ struct Phys {
   double shock_x0, shock_cot, shock_vx;   // x_s(y, t) = x0 + y cot(angle) + t speed / sin(angle)
   int shock_pre, shock_post;
   int oe, bp, k, decomp;   // decomp: 0 optimal convex decomposition, 1 classical (ZXS)
+  float gamma_f, gm1_f;    // FP32 roundings of gamma and gamma - 1 (mixed form)
 };
+
+// gamma and gamma - 1 in the working precision (no conversion in the kernels)
+template <typename Real>
+__device__ __forceinline__ Real phys_gamma(const Phys &ph) {
+  if constexpr (sizeof(Real) == sizeof(float)) return ph.gamma_f; else return ph.gamma;
+}
+template <typename Real>
+__device__ __forceinline__ Real phys_gm1(const Phys &ph) {
+  if constexpr (sizeof(Real) == sizeof(float)) return ph.gm1_f; else return ph.gamma - 1.0;
+}
 
 // Device-resident scalars of one solver.
 struct Scalars {
   double t, t_end, dt, alpha, cfl, min_ca;
   double mean[4], area_total, dev[5];
   double invD[4];   // 1 / normaliser of the damped quantities (rho, m_n|m1, m_t|m2, E); 0 if constant
+  float invDf[4];   // their FP32 roundings (mixed form)
   long long steps, limited, nonphys, breaches;
   int active, pad;
 };
@@ -467,6 +479,7 @@ __device__ __forceinline__ void write_inv_normalisers(Scalars *sc, int cw) {
     const double mnorm = sqrt(sc->mean[1] * sc->mean[1] + sc->mean[2] * sc->mean[2]);
     sc->invD[1] = sc->invD[2] = inv(sc->dev[1], mnorm);
   }
+  for (int q = 0; q < 4; ++q) sc->invDf[q] = float(sc->invD[q]);
 }
 
 // ------------------------------------------------------------------------

@@ -89,7 +89,7 @@ __device__ __forceinline__ void rk_tile(const MeshDev &m, const Phys &ph, StateD
   double mass[4] = {0.0, 0.0, 0.0, 0.0};
   if (Kc < nt) {
     const double dt = sc->dt, alpha_d = sc->alpha, t_in = sc->t + c_in * sc->dt;
-    const Real alpha = Real(alpha_d), gm1 = Real(ph.gamma - 1.0);
+    const Real alpha = Real(alpha_d), gm1 = phys_gm1<Real>(ph);
     const double area = m.area[Kc];
     const Real *gj = Geo<Real>::jinv(m);
     const Real jx = gj[Kc], jy = gj[nt + Kc], ex = gj[2 * nt + Kc], ey = gj[3 * nt + Kc];
@@ -128,6 +128,7 @@ __device__ __forceinline__ void rk_tile(const MeshDev &m, const Phys &ph, StateD
     // ---- edge term: - sum_i l_i sum_nu w_nu Fhat Psi_l -------------------------
     double acc0[4] = {0.0, 0.0, 0.0, 0.0};
     Real tv0[NQ][4];   // mixed form: per-point mode-0 contributions of one edge
+    float s_hi[4] = {0.0f, 0.0f, 0.0f, 0.0f}, s_lo[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       const int32_t cn = m.conn[i * nt + Kc];
@@ -194,13 +195,23 @@ __device__ __forceinline__ void rk_tile(const MeshDev &m, const Phys &ph, StateD
       if constexpr (sizeof(Real) != sizeof(double)) {
         // FP32 edge contributions summed in an order that is symmetric under
         // the neighbour's reversed point order, so the neighbour's sum is the
-        // exact negation; the FP64 average accumulates one term per edge
+        // exact negation.  The three edge sums are added as an unevaluated
+        // FP32 pair (Knuth's TwoSum: hi + lo holds each partial sum exactly,
+        // the last lo addition rounds at 2^-48 of the sum) on the FP32 pipe,
+        // and the FP64 average takes hi + lo once.
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-          const Real se = NQ == 3 ? (tv0[0][c] + tv0[2][c]) + tv0[1][c] : tv0[0][c] + tv0[NQ - 1][c];
-          acc0[c] -= double(se);
+          const float se = NQ == 3 ? (tv0[0][c] + tv0[2][c]) + tv0[1][c] : tv0[0][c] + tv0[NQ - 1][c];
+          const float x = -se, sum = s_hi[c] + x, bv = sum - s_hi[c];
+          const float err = (s_hi[c] - (sum - bv)) + (x - bv);
+          s_hi[c] = sum;
+          s_lo[c] += err;
         }
       }
+    }
+    if constexpr (sizeof(Real) != sizeof(double)) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc0[c] = double(s_hi[c]) + double(s_lo[c]);
     }
 
     // ---- mass inverse and SSP-RK combination -----------------------------------
@@ -231,7 +242,7 @@ __device__ __forceinline__ void rk_tile(const MeshDev &m, const Phys &ph, StateD
 
     // ---- vertex derivatives of u_h for the OE jumps ------------------------------
     Real *vo = vdo + Kc * VD_CELL;
-    const Real gamma = Real(ph.gamma);
+    const Real gamma = phys_gamma<Real>(ph);
 #pragma unroll
     for (int vv = 0; vv < 3; ++vv) {
       const double xi = vert_xi(vv), eta = vert_eta(vv);
@@ -407,7 +418,7 @@ __device__ __forceinline__ void edge_tile(const MeshDev &m, const Phys &ph, cons
   const int64_t nt = m.nt;
   const int64_t e0 = m.etile[tile], e1 = m.etile[tile + 1];
   const double t_out = sc->t + c_out * sc->dt;
-  const Real gamma = Real(ph.gamma);
+  const Real gamma = phys_gamma<Real>(ph);
   const int cw = ph.oe == 2;
   for (int64_t e = e0 + threadIdx.x; e < e1; e += TPB) {
     const int64_t Kc = m.e_cell[e];
@@ -681,7 +692,7 @@ __device__ __forceinline__ void limit_and_trace_mixed(const MeshDev &m, const Ph
                                                       long long cnt[2]) {
   constexpr int NB = Deg<K>::NB, NQ = Deg<K>::NQ, NE = 3 * NQ;
   const int64_t nt = m.nt;
-  const float gamma = float(ph.gamma), gm1 = float(ph.gamma - 1.0);
+  const float gamma = ph.gamma_f, gm1 = ph.gm1_f;
   // the two extra points of the limiter set for the FP32 screen (P1: vertices
   // v1, v2; P2: internal nodes, from the mesh's FP32 copy)
   float px[2], py[2];
@@ -711,11 +722,28 @@ __device__ __forceinline__ void limit_and_trace_mixed(const MeshDev &m, const Ph
   // reloads them)
 #pragma unroll
   for (int c = 0; c < 4; ++c) out.avg[c * nt + Kc] = a0[c];
-  const double Ebar = int_energy(a0);
-  const bool avg_ok = (a0[0] > 0.0) && (Ebar > 0.0);
-  const float eps1 = float(fmin(a0[0], 1e-13)), eps2 = float(fmin(Ebar, 1e-13));
   float a0f[4];
   to_real(a0, a0f);
+  // admissibility of the average and eps1 = min(rho, 1e-13), eps2 =
+  // min(Ebar, 1e-13) of Sec. 4.4.  An FP32 screen settles the usual case
+  // without the FP64 division: rho > 2e-13 and rho Ebar = rho E - |m|^2 / 2 >
+  // 2e-13 rho with a margin (1e-5 relative) far above the FP32 rounding of the
+  // test imply rho > 1e-13 and Ebar > 1e-13 exactly, hence eps1 = eps2 = 1e-13.
+  // Anything else (tiny, non-finite, near the bounds) takes the FP64 path.
+  bool avg_ok;
+  float eps1, eps2;
+  {
+    const float q2 = a0f[1] * a0f[1] + a0f[2] * a0f[2], pe = a0f[3] * a0f[0];
+    if (a0f[0] > 2e-13f && pe - 0.5f * q2 > 2e-13f * a0f[0] + 1e-5f * (fabsf(pe) + 0.5f * q2)) {
+      avg_ok = true;
+      eps1 = eps2 = float(1e-13);
+    } else {
+      const double Ebar = int_energy(a0);
+      avg_ok = (a0[0] > 0.0) && (Ebar > 0.0);
+      eps1 = float(fmin(a0[0], 1e-13));
+      eps2 = float(fmin(Ebar, 1e-13));
+    }
+  }
   bool lim64 = false;
   if (do_bp) {
     if (!avg_ok) {
@@ -836,7 +864,7 @@ __device__ __forceinline__ void oe_bp_tile(const MeshDev &m, const Phys &ph, Sta
   long long cnt[2] = {0, 0};
   if (Kc < nt) {
     const double dt = sc->dt, t_out = sc->t + c_out * sc->dt;
-    const Real gamma = Real(ph.gamma);
+    const Real gamma = phys_gamma<Real>(ph);
     double a0[4];
     Real hi[4][NB];
     load_state<Real, NB>(uh, nt, Kc, a0, hi);
@@ -855,7 +883,9 @@ __device__ __forceinline__ void oe_bp_tile(const MeshDev &m, const Phys &ph, Sta
       // 1 / normaliser of rho, (m_n | m1), (m_t | m2), E; 0 for a constant component
       Real iD[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) iD[q] = Real(sc->invD[q]);
+      for (int q = 0; q < 4; ++q) {
+        if constexpr (sizeof(Real) == sizeof(float)) iD[q] = sc->invDf[q]; else iD[q] = sc->invD[q];
+      }
       Real sig[4][K + 1];
 #pragma unroll
       for (int c = 0; c < 4; ++c)
@@ -993,7 +1023,7 @@ __device__ __forceinline__ void oe_bp_tile(const MeshDev &m, const Phys &ph, Sta
         }
       }
       // traces, F.n and wave speed of the limited state at the edge Gauss points
-      const Real gm1 = Real(ph.gamma - 1.0);
+      const Real gm1 = phys_gm1<Real>(ph);
   #pragma unroll
       for (int i = 0; i < 3; ++i) {
   #pragma unroll
