@@ -19,13 +19,13 @@ namespace dg {
 // instantiations).  Higher occupancy hides the latency of the neighbour
 // gathers and of the FP64 pipe better than the few spilled registers cost.
 #ifndef RK_MINB_F
-#define RK_MINB_F 5
+#define RK_MINB_F 6
 #endif
 #ifndef STATS_MINB_F
 #define STATS_MINB_F 6
 #endif
 #ifndef OEBP_MINB_F
-#define OEBP_MINB_F 4
+#define OEBP_MINB_F 6
 #endif
 #ifndef RK_MINB_D
 #define RK_MINB_D 3
