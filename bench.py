@@ -51,9 +51,19 @@ ALGO_FLOPS_P2 = {"rk": 1872.0, "stats": 652.0, "oe_bp": 1062.0}
 # (2 DFMA + DMUL + DADD from one ncu capture / cells); division, square root
 # and exp expand into DFMA sequences.  None = not re-measured since the kernel
 # last changed.
-EXECUTED_FLOPS_P2 = {"rk": 2089.0, "stats": 913.0, "oe_bp": 1435.0}
+EXECUTED_FLOPS_P2 = {"rk": 2089.0, "stats": 848.0, "oe_bp": 1435.0}
 # DRAM bytes (read + write) per launch from the same ncu capture.
-TRAFFIC_PER_LAUNCH = {"rk": 1.638e9, "stats": 0.951e9, "oe_bp": 1.320e9}
+TRAFFIC_PER_LAUNCH = {"rk": 1.637e9, "stats": 0.951e9, "oe_bp": 1.319e9}
+# Mixed form (P2, FP32 modes and geometry, FP64 averages): algorithmic HBM
+# bytes per cell-stage, each array element moved once and neighbour data
+# taken from L2.  k_rk: u_n, v and u_h (3 x 112), geometry 80, own traces 144,
+# vertex records 192, Hessians 48.  k_stats: u_h 112, vertex records and
+# Hessians 240, per edge (1.5 per cell) 4 + 1 + 4 index bytes, normal 8 and
+# the 64-byte OE record.  k_oe_bp: u_h 112, geometry and indices 88, OE
+# records 1.5 x 64, internal nodes 16, output state 112, traces 144.
+ALGO_BYTES_MIXED_P2 = {"rk": 800.0, "stats": 474.0, "oe_bp": 552.0}
+# DRAM bytes per launch of the mixed-form kernels from one ncu capture
+TRAFFIC_MIXED_PER_LAUNCH = {"rk": 0.734e9, "stats": 0.507e9, "oe_bp": 0.557e9}
 
 
 def load_peaks():
@@ -340,6 +350,17 @@ def main():
                 k2 = {k: v for k, v in prof2.items() if v[1] > 0}
                 tot2 = sum(v[0] for v in k2.values())
                 mixed["kernel_share"] = {k: round(v[0] / tot2, 4) for k, v in k2.items()}
+                # HBM roofline of the dominant mixed-form kernel
+                dom2 = max(k2, key=lambda k: k2[k][0])
+                avg2 = k2[dom2][0] / k2[dom2][1]
+                hbm = peaks.get("hbm_gbs", 6800.0)
+                if dom2 in ALGO_BYTES_MIXED_P2 and wl.k == 2:
+                    gbs = ALGO_BYTES_MIXED_P2[dom2] * nt / (avg2 / 1e3) / 1e9
+                    mixed["roofline"] = {"bound": "hbm", "kernel": dom2, "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                                         "frac": gbs / hbm, "traffic": TRAFFIC_MIXED_PER_LAUNCH.get(dom2),
+                                         "peak_source": f"{peak_src} HBM copy bandwidth",
+                                         "algorithmic_bytes_per_cell": ALGO_BYTES_MIXED_P2[dom2],
+                                         "avg_launch_ms": avg2}
             del s2
             # density L1 difference from the FP64 path after the same number of steps
             n_l1 = 20
