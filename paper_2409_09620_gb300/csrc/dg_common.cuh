@@ -260,6 +260,9 @@ __device__ __forceinline__ void flux_dir2(const T u[4], T d1x, T d1y, T d2x, T d
 // for a NaN with a clear sign bit); a plain comparison for floats
 __device__ __forceinline__ bool gt0(double x) { return __double_as_longlong(x) > 0; }
 __device__ __forceinline__ bool gt0(float x) { return x > 0.0f; }
+// x != 0 on the integer units (true for NaN, false for +0 and -0, as the comparison)
+__device__ __forceinline__ bool nonzero_bits(double x) { return (__double_as_longlong(x) << 1) != 0; }
+__device__ __forceinline__ bool nonzero_bits(float x) { return (__float_as_int(x) << 1) != 0; }
 
 // F(u) . n and the spectral radius |v.n| + c (+inf for rho <= 0) with one reciprocal
 template <typename T>

@@ -11,6 +11,8 @@
 //             maximum wave speed of the limited state at the edge Gauss points
 //             (eq. 1250) for the next stage
 #pragma once
+#include <type_traits>
+
 #include "dg_common.cuh"
 
 namespace dg {
@@ -177,10 +179,12 @@ __device__ __forceinline__ void rk_tile(const MeshDev &m, const Phys &ph, StateD
             flux_dir(up, nx, ny, gm1, fp);
           }
         }
-        const Real lw = li * Real(gauss_w(NQ, nu));
+        // l_i w_nu / 2: the 1/2 of the LF flux rides on the weight (a power of
+        // two, so the products are bitwise those of scaling the flux)
+        const Real lw = li * Real(0.5 * gauss_w(NQ, nu));
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-          const Real fh = Real(0.5) * (fm[c] + fp[c] - alpha * (up[c] - um[c]));
+          const Real fh = fm[c] + fp[c] - alpha * (up[c] - um[c]);
           const Real tv = lw * fh;
           if constexpr (sizeof(Real) == sizeof(double)) {
             acc0[c] -= double(tv);
@@ -215,30 +219,39 @@ __device__ __forceinline__ void rk_tile(const MeshDev &m, const Phys &ph, StateD
     }
 
     // ---- mass inverse and SSP-RK combination -----------------------------------
-    double un0[4];
-    Real cu[4][NB];
-    load_state<Real, NB>(un, nt, Kc, un0, cu);
     const double dta = dt * m.iarea[Kc];
-    // the stage coefficients in the working precision, converted once
-    const Real ar = Real(a), br = Real(b), dtar = Real(dta);
     double h0[4];
     Real hh[4][NB];
     Real h0r[4];
+    // a u_n + b (v + dt L(v)); the first stage (a = 0, b = 1, v = u_n) skips
+    // the zero term and the load of u_n (equal up to the sign of a zero)
+    auto combine = [&](auto first_stage) {
+      constexpr bool FIRST = decltype(first_stage)::value;
+      double un0[4] = {0.0, 0.0, 0.0, 0.0};
+      Real cu[4][NB];
+      if constexpr (!FIRST) load_state<Real, NB>(un, nt, Kc, un0, cu);
+      // the stage coefficients in the working precision, converted once
+      const Real ar = Real(a), br = Real(b), dtar = Real(dta);
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const double v0c = sizeof(Real) == sizeof(double) ? v0[c] : reload_avg(v.avg + c * nt + Kc);
-      h0[c] = a * un0[c] + b * (v0c + dta * acc0[c]);
-      uh.avg[c * nt + Kc] = h0[c];
-      mass[c] = area * h0[c];
-      h0r[c] = Real(h0[c]);
-      hh[c][0] = Real(0);
+      for (int c = 0; c < 4; ++c) {
+        const double v0c = sizeof(Real) == sizeof(double) ? v0[c] : reload_avg(v.avg + c * nt + Kc);
+        if constexpr (FIRST) h0[c] = v0c + dta * acc0[c];
+        else h0[c] = a * un0[c] + b * (v0c + dta * acc0[c]);
+        uh.avg[c * nt + Kc] = h0[c];
+        mass[c] = area * h0[c];
+        h0r[c] = Real(h0[c]);
+        hh[c][0] = Real(0);
 #pragma unroll
-      for (int l = 1; l < NB; ++l) {
-        const Real s = sizeof(Real) == sizeof(double) ? Real(dta * inv_mass_c(l)) : dtar * Real(inv_mass_c(l));
-        hh[c][l] = ar * cu[c][l] + br * (cv[c][l] + s * acc[c][l]);
-        uh.hi[(c * (NB - 1) + (l - 1)) * nt + Kc] = hh[c][l];
+        for (int l = 1; l < NB; ++l) {
+          const Real s = sizeof(Real) == sizeof(double) ? Real(dta * inv_mass_c(l)) : dtar * Real(inv_mass_c(l));
+          if constexpr (FIRST) hh[c][l] = cv[c][l] + s * acc[c][l];
+          else hh[c][l] = ar * cu[c][l] + br * (cv[c][l] + s * acc[c][l]);
+          uh.hi[(c * (NB - 1) + (l - 1)) * nt + Kc] = hh[c][l];
+        }
       }
-    }
+    };
+    if (a == 0.0 && b == 1.0) combine(std::true_type{});
+    else combine(std::false_type{});
 
     // ---- vertex derivatives of u_h for the OE jumps ------------------------------
     Real *vo = vdo + Kc * VD_CELL;
@@ -264,10 +277,10 @@ __device__ __forceinline__ void rk_tile(const MeshDev &m, const Phys &ph, StateD
       }
       // 1/rho and sound speed at the vertex, for the wave speeds beta of the OE (+inf for rho <= 0)
       Real ri = Real(0), cs = Real(INFINITY);
-      if (val4[0] > Real(0)) {
+      if (gt0(val4[0])) {
         ri = Real(1) / val4[0];
         Real p = gm1 * (val4[3] - Real(0.5) * (val4[1] * val4[1] + val4[2] * val4[2]) * ri);
-        p = p > Real(0) ? p : Real(0);
+        p = gt0(p) ? p : Real(0);
         cs = sqrt(gamma * p * ri);
       }
       rec[12] = ri;
@@ -278,6 +291,11 @@ __device__ __forceinline__ void rk_tile(const MeshDev &m, const Phys &ph, StateD
     }
     if (K == 2) {
       Real *ho = hso + Kc * 12;
+      // physical second derivatives from the reference ones: the factors of
+      // J^-T H J^-1, shared by the four components
+      const Real gxx0 = jx * jx, gxe0 = Real(2) * jx * ex, gee0 = ex * ex;
+      const Real gxx1 = jx * jy, gxe1 = jx * ey + jy * ex, gee1 = ex * ey;
+      const Real gxx2 = jy * jy, gxe2 = Real(2) * jy * ey, gee2 = ey * ey;
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         Real hxx = Real(0), hxe = Real(0), hee = Real(0);
@@ -287,9 +305,9 @@ __device__ __forceinline__ void rk_tile(const MeshDev &m, const Phys &ph, StateD
           hxe = cfma(psi_2(l, 1), hh[c][l], hxe);
           hee = cfma(psi_2(l, 2), hh[c][l], hee);
         }
-        ho[3 * c + 0] = hxx * jx * jx + Real(2) * hxe * jx * ex + hee * ex * ex;
-        ho[3 * c + 1] = hxx * jx * jy + hxe * (jx * ey + jy * ex) + hee * ex * ey;
-        ho[3 * c + 2] = hxx * jy * jy + Real(2) * hxe * jy * ey + hee * ey * ey;
+        ho[3 * c + 0] = hxx * gxx0 + hxe * gxe0 + hee * gee0;
+        ho[3 * c + 1] = hxx * gxx1 + hxe * gxe1 + hee * gee1;
+        ho[3 * c + 2] = hxx * gxx2 + hxe * gxe2 + hee * gee2;
       }
     }
   }
@@ -914,7 +932,7 @@ __device__ __forceinline__ void oe_bp_tile(const MeshDev &m, const Phys &ph, Sta
           dl[3] = Ah * iD[3] * er[ej_row(3, j, K)];
 #pragma unroll
           for (int c = 0; c < 4; ++c)
-            if (bh_finite || dl[c] != Real(0)) sig[c][j] += bh * dl[c];
+            if (bh_finite || nonzero_bits(dl[c])) sig[c][j] += bh * dl[c];
           hj *= h;
         }
       }
