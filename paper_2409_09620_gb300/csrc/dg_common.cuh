@@ -70,8 +70,8 @@ template <> struct Geo<float> {
 // are the negated values the other cell uses, bit for bit.
 template <typename Real> struct TraceStride { static constexpr int value = sizeof(Real) == 4 ? 4 : 8; };
 __host__ __device__ constexpr int trace_stride(int precision) { return precision == 0 ? 8 : 4; }
-// per-edge OE record ej[ne][EJ_STRIDE]: beta, then sqrt of the trapezoidal
-// jump sums for q = rho, (m_n|m_t max | m1), (m2), E and j = 0..k (13 used)
+// per-edge OE record ej[ne][EJ_STRIDE]: beta, then sqrt(2 J) of the trapezoidal
+// jump sums J for q = rho, (m_n|m_t max | m1), (m2), E and j = 0..k (13 used)
 constexpr int EJ_STRIDE = 16;
 __host__ __device__ constexpr int ej_row(int q, int j, int K) { return 1 + q * (K + 1) + j; }
 // per-cell vertex record vd[nt][3][VD_STRIDE]: value (4), gradient (8), 1/rho, sound speed

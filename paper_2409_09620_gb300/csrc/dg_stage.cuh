@@ -422,8 +422,8 @@ __device__ __forceinline__ void ghost_vertex(int tag, const Real val[4], const R
 
 // --------------------------------------------------------------------------
 // OE jump data of one edge, computed once for both cells that share it: beta
-// (max spectral radius of both sides at both endpoints) and the square roots
-// of the trapezoidal sums 1/2 sum_{|alpha| = j} C_j^alpha1 [d^alpha q]^2 over
+// (max spectral radius of both sides at both endpoints) and sqrt(2 J) for the
+// trapezoidal sums J = 1/2 sum_{|alpha| = j} C_j^alpha1 [d^alpha q]^2 over
 // the two endpoints (eqs. OEScalar:Coef2 with the trapezoidal rule,
 // RIOESys:Coef1/Coef2), seen from the owning cell.  Jump sums are even in the
 // sign of the jump and of the normal, so both cells share them.
@@ -516,10 +516,11 @@ __device__ __forceinline__ void edge_tile(const MeshDev &m, const Phys &ph, cons
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        Jq[q][0] += Real(0.5) * jv[q] * jv[q];
-        Jq[q][1] += Real(0.5) * (jg[q][0] * jg[q][0] + jg[q][1] * jg[q][1]);
+        // 2 J: the 1/2 of the trapezoidal rule moves into A (sqrt(1/2))
+        Jq[q][0] = fma(jv[q], jv[q], Jq[q][0]);
+        Jq[q][1] = fma(jg[q][0], jg[q][0], fma(jg[q][1], jg[q][1], Jq[q][1]));
         if (K == 2)
-          Jq[q][K] += Real(0.5) * (jh[q][0] * jh[q][0] + Real(2) * jh[q][1] * jh[q][1] + jh[q][2] * jh[q][2]);
+          Jq[q][K] = fma(jh[q][0], jh[q][0], fma(jh[q][1] + jh[q][1], jh[q][1], fma(jh[q][2], jh[q][2], Jq[q][K])));
       }
     }
     Real er[EJ_STRIDE];
@@ -904,6 +905,11 @@ __device__ __forceinline__ void oe_bp_tile(const MeshDev &m, const Phys &ph, Sta
       for (int q = 0; q < 4; ++q) {
         if constexpr (sizeof(Real) == sizeof(float)) iD[q] = sc->invDf[q]; else iD[q] = sc->invD[q];
       }
+      // sigma_q^j = sum_i (beta_i / h_i) delta_{i,q}^j with delta = A^{k,j} h^j
+      // sqrt(J) / D_q, A^{k,j} = (2j + 1) / ((2k - 1) j!).  The edge records hold
+      // sqrt(2 J), so A carries a factor sqrt(1/2); the edge sum is taken
+      // first and scaled by 1 / D_q once (a constant component, 1 / D_q = 0,
+      // gets sigma = 0).  RIOE: m2 shares the momentum sums of m1.
       Real sig[4][K + 1];
 #pragma unroll
       for (int c = 0; c < 4; ++c)
@@ -911,31 +917,33 @@ __device__ __forceinline__ void oe_bp_tile(const MeshDev &m, const Phys &ph, Sta
         for (int j = 0; j <= K; ++j) sig[c][j] = Real(0);
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        // beta and sqrt of the jump sums of this edge (edge_tile, shared by both cells)
+        // beta and sqrt(2 J) of this edge (edge_tile, shared by both cells)
         const int64_t eid = m.cedge[i * nt + Kc];
         const Real h = Geo<Real>::hgeo(m)[i * nt + Kc], ih = Geo<Real>::hgeo(m)[(3 + i) * nt + Kc];
         Real er[EJ_STRIDE];
         vload<EJ_STRIDE>(ej + eid * EJ_STRIDE, er);
         const Real bh = er[0] * ih;
-        // a zero delta adds nothing; it is skipped only when beta / h is not
+        // a zero jump adds nothing; it is skipped only when beta / h is not
         // finite (beta = +inf at a vertex with rho <= 0), where 0 * inf would be NaN
         const bool bh_finite = is_finite_bits(bh);
-        // delta_q^j = A^{k,j} h^j sqrt(J) / D_q, A^{k,j} = (2j + 1) / ((2k - 1) j!)
         Real hj = Real(1);
 #pragma unroll
         for (int j = 0; j <= K; ++j) {
-          const Real Ah = Real((2.0 * j + 1.0) / ((2.0 * K - 1.0) * (j == 2 ? 2.0 : 1.0))) * hj;
-          Real dl[4];
-          dl[0] = Ah * iD[0] * er[ej_row(0, j, K)];
-          dl[1] = Ah * iD[1] * er[ej_row(1, j, K)];
-          dl[2] = cw ? Ah * iD[2] * er[ej_row(2, j, K)] : dl[1];
-          dl[3] = Ah * iD[3] * er[ej_row(3, j, K)];
+          const Real F = bh * (Real((2.0 * j + 1.0) / ((2.0 * K - 1.0) * (j == 2 ? 2.0 : 1.0)) *
+                                    0.70710678118654752440) * hj);
 #pragma unroll
-          for (int c = 0; c < 4; ++c)
-            if (bh_finite || nonzero_bits(dl[c])) sig[c][j] += bh * dl[c];
+          for (int c = 0; c < 4; ++c) {
+            if (c == 2 && !cw) continue;
+            const Real e = er[ej_row(c, j, K)];
+            if (bh_finite || nonzero_bits(e)) sig[c][j] = fma(F, e, sig[c][j]);
+          }
           hj *= h;
         }
       }
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int j = 0; j <= K; ++j) sig[c][j] = nonzero_bits(iD[c]) ? iD[c] * sig[c][j] : Real(0);
       // exact solution of the damping ODE: mode of degree m times exp(-dt sum_{j<=m} sigma^j)
       Real fac[4][K + 1];
 #pragma unroll
@@ -1031,14 +1039,20 @@ __device__ __forceinline__ void oe_bp_tile(const MeshDev &m, const Phys &ph, Sta
       }
       // ---------------------------- output ----------------------------------------
   #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        out.avg[c * nt + Kc] = a0[c];
-        const double th = c == 0 ? th_r : th_a;
+      for (int c = 0; c < 4; ++c) out.avg[c * nt + Kc] = a0[c];
+      if (th_r < 1.0 || th_a < 1.0) {   // rare: the cell is limited
   #pragma unroll
-        for (int l = 1; l < NB; ++l) {
-          const Real val = th < 1.0 ? Real(th * double(hi[c][l])) : hi[c][l];
-          out.hi[(c * (NB - 1) + (l - 1)) * nt + Kc] = val;
+        for (int c = 0; c < 4; ++c) {
+          const double th = c == 0 ? th_r : th_a;
+  #pragma unroll
+          for (int l = 1; l < NB; ++l)
+            out.hi[(c * (NB - 1) + (l - 1)) * nt + Kc] = th < 1.0 ? Real(th * double(hi[c][l])) : hi[c][l];
         }
+      } else {
+  #pragma unroll
+        for (int c = 0; c < 4; ++c)
+  #pragma unroll
+          for (int l = 1; l < NB; ++l) out.hi[(c * (NB - 1) + (l - 1)) * nt + Kc] = hi[c][l];
       }
       // traces, F.n and wave speed of the limited state at the edge Gauss points
       const Real gm1 = phys_gm1<Real>(ph);
