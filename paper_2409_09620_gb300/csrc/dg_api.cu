@@ -62,6 +62,7 @@ struct dg_mesh {
   float *jinv_f = nullptr, *nrm_f = nullptr, *len_f = nullptr, *hgeo_f = nullptr;
   double *iarea = nullptr;
   float *node_f = nullptr;
+  double *psi_node = nullptr;
   double min_ca[4] = {0, 0, 0, 0};   // (P1 optimal, P1 ZXS, P2 optimal, P2 ZXS)
   double area_total = 0.0;
   ~dg_mesh() {
@@ -69,6 +70,7 @@ struct dg_mesh {
     cudaFree(c_area); cudaFree(limv); cudaFree(conn); cudaFree(hgeo);
     cudaFree(e_cell); cudaFree(e_loc); cudaFree(etile); cudaFree(cedge);
     cudaFree(jinv_f); cudaFree(nrm_f); cudaFree(len_f); cudaFree(hgeo_f); cudaFree(iarea); cudaFree(node_f);
+    cudaFree(psi_node);
   }
 };
 
@@ -241,6 +243,7 @@ extern "C" int32_t dg_mesh_create(int64_t nv, const double *xy, int64_t nt, cons
   MTRY(dalloc(&m->hgeo_f, 6 * nt));
   MTRY(dalloc(&m->iarea, nt));
   MTRY(dalloc(&m->node_f, 4 * nt));
+  MTRY(dalloc(&m->psi_node, 10 * nt));
   MTRY(dalloc(&m->e_cell, m->ne));
   MTRY(dalloc(&m->e_loc, m->ne));
   MTRY(dalloc(&m->etile, ntiles + 1));
@@ -254,7 +257,7 @@ extern "C" int32_t dg_mesh_create(int64_t nv, const double *xy, int64_t nt, cons
   MTRY(cudaMemcpy(m->vxy, m->vxy_host.data(), sizeof(double) * 6 * nt, cudaMemcpyHostToDevice));
   MTRY(cudaMemcpy(m->conn, conn.data(), sizeof(int32_t) * 3 * nt, cudaMemcpyHostToDevice));
   GeomPtrs g{m->area,   m->jinv,  m->nrm,   m->len,    m->hgeo, m->node, m->c_area,
-             m->limv,   m->jinv_f, m->nrm_f, m->len_f, m->hgeo_f, m->iarea, m->node_f};
+             m->limv,   m->jinv_f, m->nrm_f, m->len_f, m->hgeo_f, m->iarea, m->node_f, m->psi_node};
   launch_geometry(nullptr, nt, m->vxy, g, part, mins);
   MTRY(cudaGetLastError());
   MTRY(cudaMemcpy(m->min_ca, mins, sizeof(double) * 4, cudaMemcpyDeviceToHost));
@@ -520,7 +523,7 @@ extern "C" int32_t dg_init(const dg_mesh *mesh, const dg_config *cfg, const doub
   c.mesh = MeshDev{nt,         mesh->area, mesh->jinv,   mesh->nrm,   mesh->len,   mesh->vxy,  mesh->node,
                    mesh->hgeo, mesh->limv, mesh->conn,   mesh->ne,    mesh->e_cell, mesh->e_loc, mesh->etile,
                    mesh->cedge, mesh->jinv_f, mesh->nrm_f, mesh->len_f, mesh->hgeo_f, mesh->iarea,
-                   mesh->node_f};
+                   mesh->node_f, mesh->psi_node};
   Phys &ph = c.phys;
   std::memset(&ph, 0, sizeof(ph));
   ph.gamma = cfg->gamma;
@@ -860,7 +863,7 @@ int32_t ensure_stack_limit(size_t bytes) {
 MeshDev mesh_device_view(const dg_mesh *m) {
   return MeshDev{m->nt,   m->area,   m->jinv,  m->nrm,   m->len,    m->vxy,    m->node,  m->hgeo, m->limv,
                  m->conn, m->ne,     m->e_cell, m->e_loc, m->etile, m->cedge, m->jinv_f, m->nrm_f, m->len_f,
-                 m->hgeo_f, m->iarea, m->node_f};
+                 m->hgeo_f, m->iarea, m->node_f, m->psi_node};
 }
 
 // every boundary edge carries a tag the scalar solver handles (transmissive or

@@ -19,6 +19,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "dg_math.h"
+
 namespace dg {
 
 constexpr int TPB = 128;                 // cells per block
@@ -46,6 +48,7 @@ struct MeshDev {
   const float *jinv_f, *nrm_f, *len_f, *hgeo_f;
   const double *iarea;
   const float *node_f;     // [4][nt] FP32 copy of node (P2 internal limiter nodes)
+  const double *psi_node;  // [2][5][nt] P2 basis psi_1..psi_5 at the two internal nodes
 };
 
 // geometry in the working precision of a kernel
@@ -260,6 +263,12 @@ __device__ __forceinline__ void flux_dir2(const T u[4], T d1x, T d1y, T d2x, T d
 // for a NaN with a clear sign bit); a plain comparison for floats
 __device__ __forceinline__ bool gt0(double x) { return __double_as_longlong(x) > 0; }
 __device__ __forceinline__ bool gt0(float x) { return x > 0.0f; }
+// exp(-x), x >= 0 (or NaN): small FP64 arguments, the usual case of the OE
+// damping away from discontinuities, take a 7-FMA Taylor polynomial
+// (dg_math.h); the rest, and FP32, the library exp
+__device__ __forceinline__ double exp_neg(double x) { return x <= EXP_NEG_SMALL_MAX ? exp_neg_small(x) : exp(-x); }
+__device__ __forceinline__ float exp_neg(float x) { return expf(-x); }
+
 // x != 0 on the integer units (true for NaN, false for +0 and -0, as the comparison)
 __device__ __forceinline__ bool nonzero_bits(double x) { return (__double_as_longlong(x) << 1) != 0; }
 __device__ __forceinline__ bool nonzero_bits(float x) { return (__float_as_int(x) << 1) != 0; }

@@ -15,6 +15,7 @@ struct GeomPtrs {
   float *jinv_f, *nrm_f, *len_f, *hgeo_f;
   double *iarea;
   float *node_f;
+  double *psi_node;
 };
 
 // a modal state: FP64 averages [4][nt] + higher modes [4][nb-1][nt] (double or float)

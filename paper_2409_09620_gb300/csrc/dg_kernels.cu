@@ -21,7 +21,7 @@ __global__ void __launch_bounds__(TPB) k_geometry(int64_t nt, const double *__re
                                                   double *jinv, double *nrm, double *len, double *hgeo,
                                                   double *node, int8_t *limv, double *c_area, double *part_min,
                                                   float *jinv_f, float *nrm_f, float *len_f, float *hgeo_f,
-                                                  double *iarea, float *node_f) {
+                                                  double *iarea, float *node_f, double *psi_node) {
   const int64_t K = (int64_t)blockIdx.x * TPB + threadIdx.x;
   double mins[4] = {INFINITY, INFINITY, INFINITY, INFINITY};
   if (K < nt) {
@@ -82,6 +82,9 @@ __global__ void __launch_bounds__(TPB) k_geometry(int64_t nt, const double *__re
       }
       node[(2 * s) * nt + K] = bary[1];
       node[(2 * s + 1) * nt + K] = bary[2];
+      // the P2 basis at the node, for the FP64 limiter
+#pragma unroll
+      for (int l = 1; l < 6; ++l) psi_node[(5 * s + l - 1) * nt + K] = psi(l, bary[1], bary[2]);
     }
     iarea[K] = 1.0 / ar;
 #pragma unroll
@@ -158,7 +161,7 @@ void launch_geometry(cudaStream_t s, int64_t nt, const double *vxy, const GeomPt
                      double *out_min4) {
   const unsigned nb = nblocks(nt);
   k_geometry<<<nb, TPB, 0, s>>>(nt, vxy, g.area, g.jinv, g.nrm, g.len, g.hgeo, g.node, g.limv, g.c_area, part_min,
-                                g.jinv_f, g.nrm_f, g.len_f, g.hgeo_f, g.iarea, g.node_f);
+                                g.jinv_f, g.nrm_f, g.len_f, g.hgeo_f, g.iarea, g.node_f, g.psi_node);
   k_fin_min4<<<1, FIN_THREADS, 0, s>>>(part_min, (int)nb, out_min4);
 }
 

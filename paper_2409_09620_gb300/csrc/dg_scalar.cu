@@ -329,7 +329,7 @@ __global__ void __launch_bounds__(TPB) k_sc_oe(MeshDev m, ScPhys ph, const doubl
 #pragma unroll
       for (int md = 1; md <= K; ++md) {
         sacc += sig[md];
-        fac[md] = exp(-dt * sacc);
+        fac[md] = exp_neg(dt * sacc);
       }
 #pragma unroll
       for (int l = 1; l < NB; ++l) c[l] *= fac[sc_degree(l)];

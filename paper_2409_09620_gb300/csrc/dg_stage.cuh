@@ -957,7 +957,7 @@ __device__ __forceinline__ void oe_bp_tile(const MeshDev &m, const Phys &ph, Sta
 #pragma unroll
         for (int md = 1; md <= K; ++md) {
           sacc += sig[c][md];
-          fac[c][md] = exp(-Real(dt) * sacc);
+          fac[c][md] = exp_neg(Real(dt) * sacc);
         }
       }
 #pragma unroll
@@ -985,23 +985,32 @@ __device__ __forceinline__ void oe_bp_tile(const MeshDev &m, const Phys &ph, Sta
         }
       double th_r = 1.0, th_a = 1.0;
       if (do_bp) {
-        double px[2], py[2];
-        if (K == 1) {
-          const int v1 = m.limv[Kc], v2 = m.limv[nt + Kc];
-          px[0] = vert_xi(v1); py[0] = vert_eta(v1); px[1] = vert_xi(v2); py[1] = vert_eta(v2);
-        } else {
-          px[0] = m.node[Kc]; py[0] = m.node[nt + Kc]; px[1] = m.node[2 * nt + Kc]; py[1] = m.node[3 * nt + Kc];
-        }
         if (ph.decomp) {
           zxs_extra_points<K, double, NE + 2>(dev);
         } else {
+          // P1: the vertices v1, v2; P2: the internal nodes, whose basis
+          // values the mesh holds
+          double psx[2][NB];
+          if (K == 1) {
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+              const int vp = m.limv[p * nt + Kc];
+#pragma unroll
+              for (int l = 1; l < NB; ++l) psx[p][l] = psi(l, vert_xi(vp), vert_eta(vp));
+            }
+          } else {
+#pragma unroll
+            for (int p = 0; p < 2; ++p)
+#pragma unroll
+              for (int l = 1; l < NB; ++l) psx[p][l] = m.psi_node[(5 * p + l - 1) * nt + Kc];
+          }
   #pragma unroll
           for (int p = 0; p < 2; ++p)
   #pragma unroll
             for (int c = 0; c < 4; ++c) {
               double s = 0.0;
   #pragma unroll
-              for (int l = 1; l < NB; ++l) s = fma(psi(l, px[p], py[p]), double(hi[c][l]), s);
+              for (int l = 1; l < NB; ++l) s = fma(psx[p][l], double(hi[c][l]), s);
               dev[NE + p][c] = s;
             }
         }
