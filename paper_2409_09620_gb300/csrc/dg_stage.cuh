@@ -290,7 +290,7 @@ __device__ __forceinline__ void rk_tile(const MeshDev &m, const Phys &ph, StateD
       vstore<VD_STRIDE>(vo + vv * VD_STRIDE, rec);
     }
     if (K == 2) {
-      Real *ho = hso + Kc * 12;
+      Real ho[12];
       // physical second derivatives from the reference ones: the factors of
       // J^-T H J^-1, shared by the four components
       const Real gxx0 = jx * jx, gxe0 = Real(2) * jx * ex, gee0 = ex * ex;
@@ -309,6 +309,7 @@ __device__ __forceinline__ void rk_tile(const MeshDev &m, const Phys &ph, StateD
         ho[3 * c + 1] = hxx * gxx1 + hxe * gxe1 + hee * gee1;
         ho[3 * c + 2] = hxx * gxx2 + hxe * gxe2 + hee * gee2;
       }
+      vstore<12>(hso + Kc * 12, ho);   // 16-byte vector stores
     }
   }
   block_reduce<4>(mass, part_sum + 4 * tile, OpSum());
@@ -446,14 +447,16 @@ __device__ __forceinline__ void edge_tile(const MeshDev &m, const Phys &ph, cons
     const Real *vme = vdi + Kc * VD_CELL;
     Real hme[12], hot[12];
 #pragma unroll
-    for (int q = 0; q < 12; ++q) hme[q] = (K == 2) ? hsi[Kc * 12 + q] : Real(0);
+    for (int q = 0; q < 12; ++q) hme[q] = Real(0);
+    if (K == 2) vload<12>(hsi + Kc * 12, hme);
     const Real *vnb = nullptr;
     int jn = 0;
     if (cn >= 0) {
       vnb = vdi + (int64_t)(cn >> 2) * VD_CELL;
       jn = cn & 3;
 #pragma unroll
-      for (int q = 0; q < 12; ++q) hot[q] = (K == 2) ? hsi[(int64_t)(cn >> 2) * 12 + q] : Real(0);
+      for (int q = 0; q < 12; ++q) hot[q] = Real(0);
+      if (K == 2) vload<12>(hsi + (int64_t)(cn >> 2) * 12, hot);
     }
     Real Jq[4][K + 1];
 #pragma unroll
