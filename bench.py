@@ -41,19 +41,20 @@ UNIT = "cell-stage updates/s"
 # counted from the kernel source: add / sub / mul = 1 flop, fma = 2, one flop
 # for each division, square root and exponential, coefficients that are zero
 # at the fixed quadrature points skipped.  k_rk: volume evaluation 208, volume
-# fluxes 186, volume accumulation 240, edge terms 565, mass inverse and RK
-# combination 150, vertex records 361, Hessians 156, block sums 6.  k_stats:
-# deviations at the volume points 236, edge OE records 277 per edge x 1.5.
-# k_oe_bp: sigma 141, damping 38, limiter at the 11 points 595, traces and
-# wave speeds 288.
-ALGO_FLOPS_P2 = {"rk": 1872.0, "stats": 652.0, "oe_bp": 1062.0}
+# fluxes 186, volume accumulation 240, edge terms 529, mass inverse and RK
+# combination 126 (mean of the three stages; the first has no u_n term),
+# vertex records 361, Hessians 126, block sums 6.  k_stats: deviations at the
+# volume points 236, edge OE records 253 per edge x 1.5.  k_oe_bp: sigma 87,
+# damping 38, limiter at the 11 points 595, traces and wave speeds 288.
+ALGO_FLOPS_P2 = {"rk": 1782.0, "stats": 616.0, "oe_bp": 1008.0}
 # FP64 flops per cell-stage the hardware executed for the same kernels
-# (2 DFMA + DMUL + DADD from one ncu capture / cells); division, square root
-# and exp expand into DFMA sequences.  None = not re-measured since the kernel
-# last changed.
-EXECUTED_FLOPS_P2 = {"rk": 2089.0, "stats": 848.0, "oe_bp": 1435.0}
-# DRAM bytes (read + write) per launch from the same ncu capture.
-TRAFFIC_PER_LAUNCH = {"rk": 1.637e9, "stats": 0.951e9, "oe_bp": 1.319e9}
+# (2 DFMA + DMUL + DADD from ncu captures / cells; k_rk: mean of its three
+# stages 1963 / 2035 / 2035); division, square root and exp expand into
+# DFMA sequences.  None = not re-measured since the kernel last changed.
+EXECUTED_FLOPS_P2 = {"rk": 2011.0, "stats": 812.0, "oe_bp": 1228.0}
+# DRAM bytes (read + write) per launch from the same captures (k_rk: mean of
+# its stages 1.596 / 1.806 / 1.806 GB).
+TRAFFIC_PER_LAUNCH = {"rk": 1.736e9, "stats": 0.951e9, "oe_bp": 1.371e9}
 # Mixed form (P2, FP32 modes and geometry, FP64 averages): algorithmic HBM
 # bytes per cell-stage, each array element moved once and neighbour data
 # taken from L2.  k_rk: u_n, v and u_h (3 x 112), geometry 80, own traces 144,
@@ -63,7 +64,7 @@ TRAFFIC_PER_LAUNCH = {"rk": 1.637e9, "stats": 0.951e9, "oe_bp": 1.319e9}
 # records 1.5 x 64, internal nodes 16, output state 112, traces 144.
 ALGO_BYTES_MIXED_P2 = {"rk": 800.0, "stats": 474.0, "oe_bp": 552.0}
 # DRAM bytes per launch of the mixed-form kernels from one ncu capture
-TRAFFIC_MIXED_PER_LAUNCH = {"rk": 0.734e9, "stats": 0.507e9, "oe_bp": 0.557e9}
+TRAFFIC_MIXED_PER_LAUNCH = {"rk": 0.714e9, "stats": 0.499e9, "oe_bp": 0.552e9}
 
 
 def load_peaks():
