@@ -254,21 +254,48 @@ __device__ __forceinline__ void rk_tile(const MeshDev &m, const Phys &ph, StateD
     else combine(std::false_type{});
 
     // ---- vertex derivatives of u_h for the OE jumps ------------------------------
+    // u_h is a polynomial of degree K in the reference coordinates, so with
+    // its value u0, reference gradient (gx0, ge0) at vertex 0 = (0, 0) and its
+    // (constant) reference Hessian (hxx, hxe, hee):
+    //   vertex 1 = (1, 0): u0 + gx0 + hxx / 2, gradient (gx0 + hxx, ge0 + hxe)
+    //   vertex 2 = (0, 1): u0 + ge0 + hee / 2, gradient (gx0 + hxe, ge0 + hee)
+    Real u0[4], gx0[4], ge0[4], hxx[4], hxe[4], hee[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      u0[c] = h0r[c];
+      gx0[c] = Real(0);
+      ge0[c] = Real(0);
+      hxx[c] = Real(0);
+      hxe[c] = Real(0);
+      hee[c] = Real(0);
+#pragma unroll
+      for (int l = 1; l < NB; ++l) {
+        u0[c] = cfma(psi(l, 0.0, 0.0), hh[c][l], u0[c]);
+        gx0[c] = cfma(psi_x(l, 0.0, 0.0), hh[c][l], gx0[c]);
+        ge0[c] = cfma(psi_y(l, 0.0, 0.0), hh[c][l], ge0[c]);
+      }
+#pragma unroll
+      for (int l = 3; l < NB; ++l) {
+        hxx[c] = cfma(psi_2(l, 0), hh[c][l], hxx[c]);
+        hxe[c] = cfma(psi_2(l, 1), hh[c][l], hxe[c]);
+        hee[c] = cfma(psi_2(l, 2), hh[c][l], hee[c]);
+      }
+    }
     Real *vo = vdo + Kc * VD_CELL;
     const Real gamma = phys_gamma<Real>(ph);
 #pragma unroll
     for (int vv = 0; vv < 3; ++vv) {
-      const double xi = vert_xi(vv), eta = vert_eta(vv);
       Real rec[VD_STRIDE];
       Real val4[4];
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        Real val = h0r[c], gx = Real(0), ge = Real(0);
-#pragma unroll
-        for (int l = 1; l < NB; ++l) {
-          val = cfma(psi(l, xi, eta), hh[c][l], val);
-          gx = cfma(psi_x(l, xi, eta), hh[c][l], gx);
-          ge = cfma(psi_y(l, xi, eta), hh[c][l], ge);
+        Real val, gx, ge;
+        if (vv == 0) {
+          val = u0[c]; gx = gx0[c]; ge = ge0[c];
+        } else if (vv == 1) {
+          val = fma(Real(0.5), hxx[c], u0[c] + gx0[c]); gx = gx0[c] + hxx[c]; ge = ge0[c] + hxe[c];
+        } else {
+          val = fma(Real(0.5), hee[c], u0[c] + ge0[c]); gx = gx0[c] + hxe[c]; ge = ge0[c] + hee[c];
         }
         val4[c] = val;
         rec[c] = val;
@@ -298,16 +325,9 @@ __device__ __forceinline__ void rk_tile(const MeshDev &m, const Phys &ph, StateD
       const Real gxx2 = jy * jy, gxe2 = Real(2) * jy * ey, gee2 = ey * ey;
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        Real hxx = Real(0), hxe = Real(0), hee = Real(0);
-#pragma unroll
-        for (int l = 3; l < NB; ++l) {
-          hxx = cfma(psi_2(l, 0), hh[c][l], hxx);
-          hxe = cfma(psi_2(l, 1), hh[c][l], hxe);
-          hee = cfma(psi_2(l, 2), hh[c][l], hee);
-        }
-        ho[3 * c + 0] = hxx * gxx0 + hxe * gxe0 + hee * gee0;
-        ho[3 * c + 1] = hxx * gxx1 + hxe * gxe1 + hee * gee1;
-        ho[3 * c + 2] = hxx * gxx2 + hxe * gxe2 + hee * gee2;
+        ho[3 * c + 0] = hxx[c] * gxx0 + hxe[c] * gxe0 + hee[c] * gee0;
+        ho[3 * c + 1] = hxx[c] * gxx1 + hxe[c] * gxe1 + hee[c] * gee1;
+        ho[3 * c + 2] = hxx[c] * gxx2 + hxe[c] * gxe2 + hee[c] * gee2;
       }
       vstore<12>(hso + Kc * 12, ho);   // 16-byte vector stores
     }
