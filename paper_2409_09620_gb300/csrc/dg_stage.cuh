@@ -514,6 +514,9 @@ __device__ __forceinline__ void edge_tile(const MeshDev &m, const Phys &ph, cons
         r_oth = cn >= -2 ? r_own : wave_speed(xv, nx, ny, gamma);
       }
       beta = max_nn(beta, max_nn(r_own, r_oth));
+      // the Hessians of P2 polynomials (and of every ghost) are constant, so
+      // the Hessian jump is the same at both endpoints: taken at v_c only
+      const bool hess = K == 2 && ev == 0;
       Real jv[4], jg[4][2], jh[4][3];
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
@@ -521,7 +524,7 @@ __device__ __forceinline__ void edge_tile(const MeshDev &m, const Phys &ph, cons
         jg[c][0] = grd[2 * c] - xg[2 * c];
         jg[c][1] = grd[2 * c + 1] - xg[2 * c + 1];
 #pragma unroll
-        for (int r = 0; r < 3; ++r) jh[c][r] = hme[3 * c + r] - xh[3 * c + r];
+        for (int r = 0; r < 3; ++r) jh[c][r] = hess ? hme[3 * c + r] - xh[3 * c + r] : Real(0);
       }
       if (!cw) {   // rotate the momentum jumps to (m_n, m_t) with the owner's normal
         Real t0 = jv[1], t1 = jv[2];
@@ -531,10 +534,12 @@ __device__ __forceinline__ void edge_tile(const MeshDev &m, const Phys &ph, cons
           t0 = jg[1][d]; t1 = jg[2][d];
           jg[1][d] = t0 * nx + t1 * ny; jg[2][d] = -t0 * ny + t1 * nx;
         }
+        if (hess) {
 #pragma unroll
-        for (int r = 0; r < 3; ++r) {
-          t0 = jh[1][r]; t1 = jh[2][r];
-          jh[1][r] = t0 * nx + t1 * ny; jh[2][r] = -t0 * ny + t1 * nx;
+          for (int r = 0; r < 3; ++r) {
+            t0 = jh[1][r]; t1 = jh[2][r];
+            jh[1][r] = t0 * nx + t1 * ny; jh[2][r] = -t0 * ny + t1 * nx;
+          }
         }
       }
 #pragma unroll
@@ -542,8 +547,10 @@ __device__ __forceinline__ void edge_tile(const MeshDev &m, const Phys &ph, cons
         // 2 J: the 1/2 of the trapezoidal rule moves into A (sqrt(1/2))
         Jq[q][0] = fma(jv[q], jv[q], Jq[q][0]);
         Jq[q][1] = fma(jg[q][0], jg[q][0], fma(jg[q][1], jg[q][1], Jq[q][1]));
-        if (K == 2)
-          Jq[q][K] = fma(jh[q][0], jh[q][0], fma(jh[q][1] + jh[q][1], jh[q][1], fma(jh[q][2], jh[q][2], Jq[q][K])));
+        if (hess) {   // both endpoints: twice the one value
+          const Real f = fma(jh[q][0], jh[q][0], fma(jh[q][1] + jh[q][1], jh[q][1], jh[q][2] * jh[q][2]));
+          Jq[q][K] = f + f;
+        }
       }
     }
     Real er[EJ_STRIDE];
