@@ -37,24 +37,26 @@ if ROOT not in sys.path:
 METRIC = "P2 Euler DG cell-stage updates/s (FP64 vs FP32), HBM GB/s; p50/p99 solve latency"
 UNIT = "cell-stage updates/s"
 
-# Algorithmic FP64 work per cell-stage of each kernel kind (P2 interior cell),
-# counted from the kernel source: add / sub / mul = 1 flop, fma = 2, one flop
-# for each division, square root and exponential, coefficients that are zero
-# at the fixed quadrature points skipped.  k_rk: volume evaluation 208, volume
-# fluxes 186, volume accumulation 240, edge terms 529, mass inverse and RK
-# combination 126 (mean of the three stages; the first has no u_n term),
-# vertex records 361, Hessians 126, block sums 6.  k_stats: deviations at the
-# volume points 236, edge OE records 253 per edge x 1.5.  k_oe_bp: sigma 87,
-# damping 38, limiter at the 11 points 595, traces and wave speeds 288.
-ALGO_FLOPS_P2 = {"rk": 1782.0, "stats": 616.0, "oe_bp": 1008.0}
+# Algorithmic FP64 work per cell-stage of each kernel kind (P2 interior cell,
+# RIOE, limiter on, cell not limited), counted from the kernel source: add /
+# sub / mul / division / square root / exponential = 1 flop, fma = 2; a
+# compile-time coefficient of 0 costs nothing and one of +-1 a single add; the
+# first term into a zero accumulator is one multiply.  k_rk: volume evaluation
+# 208, volume fluxes 186, volume accumulation 368, edge terms 529, mass
+# inverse and RK combination 106 (mean of the three stages; the first has no
+# u_n term), vertex records 269, Hessians 73, block sums 6.  k_stats:
+# deviations at the volume points 231, edge OE records 187 per edge x 1.5.
+# k_oe_bp: sigma 87, damping 38, limiter at the 11 points 497, traces and
+# wave speeds 297.
+ALGO_FLOPS_P2 = {"rk": 1745.0, "stats": 512.0, "oe_bp": 919.0}
 # FP64 flops per cell-stage the hardware executed for the same kernels
 # (2 DFMA + DMUL + DADD from ncu captures / cells; k_rk: mean of its three
-# stages 1963 / 2035 / 2035); division, square root and exp expand into
+# stages 1891 / 1963 / 1963); division, square root and exp expand into
 # DFMA sequences.  None = not re-measured since the kernel last changed.
-EXECUTED_FLOPS_P2 = {"rk": 2011.0, "stats": 812.0, "oe_bp": 1228.0}
+EXECUTED_FLOPS_P2 = {"rk": 1939.0, "stats": 737.0, "oe_bp": 1228.0}
 # DRAM bytes (read + write) per launch from the same captures (k_rk: mean of
-# its stages 1.596 / 1.806 / 1.806 GB).
-TRAFFIC_PER_LAUNCH = {"rk": 1.736e9, "stats": 0.951e9, "oe_bp": 1.371e9}
+# its stages 1.595 / 1.804 / 1.805 GB).
+TRAFFIC_PER_LAUNCH = {"rk": 1.735e9, "stats": 0.947e9, "oe_bp": 1.371e9}
 # Mixed form (P2, FP32 modes and geometry, FP64 averages): algorithmic HBM
 # bytes per cell-stage, each array element moved once and neighbour data
 # taken from L2.  k_rk: u_n, v and u_h (3 x 112), geometry 80, own traces 144,
@@ -64,7 +66,7 @@ TRAFFIC_PER_LAUNCH = {"rk": 1.736e9, "stats": 0.951e9, "oe_bp": 1.371e9}
 # records 1.5 x 64, internal nodes 16, output state 112, traces 144.
 ALGO_BYTES_MIXED_P2 = {"rk": 800.0, "stats": 474.0, "oe_bp": 552.0}
 # DRAM bytes per launch of the mixed-form kernels from one ncu capture
-TRAFFIC_MIXED_PER_LAUNCH = {"rk": 0.714e9, "stats": 0.499e9, "oe_bp": 0.552e9}
+TRAFFIC_MIXED_PER_LAUNCH = {"rk": 0.712e9, "stats": 0.495e9, "oe_bp": 0.554e9}
 
 
 def load_peaks():
