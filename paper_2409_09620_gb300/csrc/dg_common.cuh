@@ -168,12 +168,13 @@ __host__ __device__ constexpr double psi_y(int l, double x, double y) {   // d/d
 // the same basis evaluated in the arithmetic of T at run-time points
 template <typename T>
 __device__ __forceinline__ T psi_t(int l, T x, T y) {
+  // nested forms with explicit fmas (see fdot2)
   return l == 0 ? T(1)
-       : l == 1 ? T(4) * x + T(2) * y - T(2)
-       : l == 2 ? T(3) * y - T(1)
-       : l == 3 ? T(24) * x * x + T(24) * x * y + T(4) * y * y - T(24) * x - T(8) * y + T(4)
-       : l == 4 ? T(20) * x * y + T(10) * y * y - T(4) * x - T(12) * y + T(2)
-                : T(10) * y * y - T(8) * y + T(1);
+       : l == 1 ? fma(T(4), x, fma(T(2), y, T(-2)))
+       : l == 2 ? fma(T(3), y, T(-1))
+       : l == 3 ? fma(x, fma(T(24), x, fma(T(24), y, T(-24))), fma(y, fma(T(4), y, T(-8)), T(4)))
+       : l == 4 ? fma(x, fma(T(20), y, T(-4)), fma(y, fma(T(10), y, T(-12)), T(2)))
+                : fma(y, fma(T(10), y, T(-8)), T(1));
 }
 // second reference derivatives: r = 0 (xi xi), 1 (xi eta), 2 (eta eta)
 __host__ __device__ constexpr double psi_2(int l, int r) {
@@ -233,12 +234,21 @@ __device__ __forceinline__ T cfma(double c, T x, T acc) {
 // ------------------------------------------------------------------------
 // Euler physics (eq. euler, G:Euler)
 // ------------------------------------------------------------------------
+// a b + c d with the fused product fixed: c d rounds, a b fuses into the
+// sum.  Left to the compiler, which product of a two-product sum is fused
+// depends on the surrounding code, so the same source inlined into two
+// kernels could round differently; every such sum on the shared stage paths
+// is written with fdot2 (or an explicit fma) so that all kernels agree bit
+// for bit.
+template <typename T>
+__device__ __forceinline__ T fdot2(T a, T b, T c, T d) { return fma(a, b, c * d); }
+
 // F(u) . d for any direction d (not necessarily unit); returns pressure.
 template <typename T>
 __device__ __forceinline__ T flux_dir(const T u[4], T dx, T dy, T gm1, T f[4]) {
   const T ri = T(1) / u[0];
-  const T p = gm1 * (u[3] - T(0.5) * (u[1] * u[1] + u[2] * u[2]) * ri);
-  const T md = u[1] * dx + u[2] * dy;
+  const T p = gm1 * (u[3] - T(0.5) * fdot2(u[1], u[1], u[2], u[2]) * ri);
+  const T md = fdot2(u[1], dx, u[2], dy);
   const T vd = md * ri;
   f[0] = md;
   f[1] = fma(u[1], vd, p * dx);
@@ -251,10 +261,10 @@ __device__ __forceinline__ T flux_dir(const T u[4], T dx, T dy, T gm1, T f[4]) {
 template <typename T>
 __device__ __forceinline__ void flux_dir2(const T u[4], T d1x, T d1y, T d2x, T d2y, T gm1, T f1[4], T f2[4]) {
   const T ri = T(1) / u[0];
-  const T p = gm1 * (u[3] - T(0.5) * (u[1] * u[1] + u[2] * u[2]) * ri);
+  const T p = gm1 * (u[3] - T(0.5) * fdot2(u[1], u[1], u[2], u[2]) * ri);
   const T ep = u[3] + p;
-  const T m1 = u[1] * d1x + u[2] * d1y, v1 = m1 * ri;
-  const T m2 = u[1] * d2x + u[2] * d2y, v2 = m2 * ri;
+  const T m1 = fdot2(u[1], d1x, u[2], d1y), v1 = m1 * ri;
+  const T m2 = fdot2(u[1], d2x, u[2], d2y), v2 = m2 * ri;
   f1[0] = m1; f1[1] = fma(u[1], v1, p * d1x); f1[2] = fma(u[2], v1, p * d1y); f1[3] = ep * v1;
   f2[0] = m2; f2[1] = fma(u[1], v2, p * d2x); f2[2] = fma(u[2], v2, p * d2y); f2[3] = ep * v2;
 }
@@ -277,8 +287,8 @@ __device__ __forceinline__ bool nonzero_bits(float x) { return (__float_as_int(x
 template <typename T>
 __device__ __forceinline__ T flux_speed(const T u[4], T nx, T ny, T gm1, T gamma, T f[4]) {
   const T ri = T(1) / u[0];
-  const T p = gm1 * (u[3] - T(0.5) * (u[1] * u[1] + u[2] * u[2]) * ri);
-  const T mn = u[1] * nx + u[2] * ny;
+  const T p = gm1 * (u[3] - T(0.5) * fdot2(u[1], u[1], u[2], u[2]) * ri);
+  const T mn = fdot2(u[1], nx, u[2], ny);
   const T vn = mn * ri;
   f[0] = mn;
   f[1] = fma(u[1], vn, p * nx);
@@ -294,13 +304,13 @@ template <typename T>
 __device__ __forceinline__ T wave_speed(const T u[4], T nx, T ny, T gamma) {
   if (!gt0(u[0])) return T(INFINITY);
   const T ri = T(1) / u[0];
-  T p = (gamma - T(1)) * (u[3] - T(0.5) * (u[1] * u[1] + u[2] * u[2]) * ri);
+  T p = (gamma - T(1)) * (u[3] - T(0.5) * fdot2(u[1], u[1], u[2], u[2]) * ri);
   p = gt0(p) ? p : T(0);
-  return fabs(u[1] * nx + u[2] * ny) * ri + sqrt(gamma * p * ri);
+  return fma(fabs(fdot2(u[1], nx, u[2], ny)), ri, sqrt(gamma * p * ri));
 }
 
 __device__ __forceinline__ double int_energy(const double u[4]) {
-  return u[3] - 0.5 * (u[1] * u[1] + u[2] * u[2]) / u[0];
+  return u[3] - 0.5 * fdot2(u[1], u[1], u[2], u[2]) / u[0];
 }
 
 // exterior state of a boundary edge (tag > 0) at physical point (px, py), time t
@@ -308,7 +318,7 @@ template <typename T>
 __device__ __forceinline__ void ghost_state(int tag, const T um[4], T nx, T ny, double px, double py, double t,
                                             const Phys &ph, T up[4]) {
   if (tag == 1) {                       // reflecting wall
-    const T mn = um[1] * nx + um[2] * ny;
+    const T mn = fdot2(um[1], nx, um[2], ny);
     up[0] = um[0];
     up[1] = um[1] - T(2) * mn * nx;
     up[2] = um[2] - T(2) * mn * ny;
@@ -317,7 +327,7 @@ __device__ __forceinline__ void ghost_state(int tag, const T um[4], T nx, T ny, 
 #pragma unroll
     for (int c = 0; c < 4; ++c) up[c] = T(ph.bc[tag - 3][c]);
   } else if (tag == 7) {                // moving shock
-    const double xs = ph.shock_x0 + py * ph.shock_cot + t * ph.shock_vx;
+    const double xs = fma(py, ph.shock_cot, fma(t, ph.shock_vx, ph.shock_x0));
     const int s = px < xs ? ph.shock_post : ph.shock_pre;
 #pragma unroll
     for (int c = 0; c < 4; ++c) up[c] = T(ph.bc[s][c]);
@@ -488,7 +498,7 @@ __device__ __forceinline__ void write_inv_normalisers(Scalars *sc, int cw) {
     sc->invD[1] = inv(sc->dev[3], fabs(sc->mean[1]));
     sc->invD[2] = inv(sc->dev[4], fabs(sc->mean[2]));
   } else {
-    const double mnorm = sqrt(sc->mean[1] * sc->mean[1] + sc->mean[2] * sc->mean[2]);
+    const double mnorm = sqrt(fdot2(sc->mean[1], sc->mean[1], sc->mean[2], sc->mean[2]));
     sc->invD[1] = sc->invD[2] = inv(sc->dev[1], mnorm);
   }
   for (int q = 0; q < 4; ++q) sc->invDf[q] = float(sc->invD[q]);

@@ -53,7 +53,7 @@ struct Request {
 size_t solve_bytes(int64_t nt, int k, int prec) {
   const size_t rs = prec == DG_PREC_MIXED ? 4 : 8;
   const size_t nb = k == 1 ? 3 : 6, nq = k == 1 ? 2 : 3;
-  const size_t mesh = 35 * 8 + 19 * 4 + 2 + 12 + 4 * 3 + 4 * 2;   // geometry (FP64 + FP32 copies), connectivity, edges
+  const size_t mesh = 45 * 8 + 23 * 4 + 2 + 12 + 4 * 3 + 4 * 2;   // geometry (FP64 + FP32 copies), connectivity, edges
   const size_t state = 3 * (4 * 8 + rs * 4 * (nb - 1));
   const size_t exch = rs * (3 * nq * trace_stride(prec) + 48 + 12 + 2 * 16);   // traces, vertex records, Hessians, ~1.5 edge records
   const size_t part = 10 * 8 + 16;   // per 128-cell block, rounded up per cell below

@@ -236,7 +236,7 @@ __device__ __forceinline__ void rk_tile(const MeshDev &m, const Phys &ph, StateD
       for (int c = 0; c < 4; ++c) {
         const double v0c = sizeof(Real) == sizeof(double) ? v0[c] : reload_avg(v.avg + c * nt + Kc);
         if constexpr (FIRST) h0[c] = v0c + dta * acc0[c];
-        else h0[c] = a * un0[c] + b * (v0c + dta * acc0[c]);
+        else h0[c] = fdot2(a, un0[c], b, fma(dta, acc0[c], v0c));
         uh.avg[c * nt + Kc] = h0[c];
         mass[c] = area * h0[c];
         h0r[c] = Real(h0[c]);
@@ -244,8 +244,8 @@ __device__ __forceinline__ void rk_tile(const MeshDev &m, const Phys &ph, StateD
 #pragma unroll
         for (int l = 1; l < NB; ++l) {
           const Real s = sizeof(Real) == sizeof(double) ? Real(dta * inv_mass_c(l)) : dtar * Real(inv_mass_c(l));
-          if constexpr (FIRST) hh[c][l] = cv[c][l] + s * acc[c][l];
-          else hh[c][l] = ar * cu[c][l] + br * (cv[c][l] + s * acc[c][l]);
+          if constexpr (FIRST) hh[c][l] = fma(s, acc[c][l], cv[c][l]);
+          else hh[c][l] = fdot2(ar, cu[c][l], br, fma(s, acc[c][l], cv[c][l]));
           uh.hi[(c * (NB - 1) + (l - 1)) * nt + Kc] = hh[c][l];
         }
       }
@@ -299,14 +299,14 @@ __device__ __forceinline__ void rk_tile(const MeshDev &m, const Phys &ph, StateD
         }
         val4[c] = val;
         rec[c] = val;
-        rec[4 + 2 * c] = gx * jx + ge * ex;
-        rec[5 + 2 * c] = gx * jy + ge * ey;
+        rec[4 + 2 * c] = fdot2(gx, jx, ge, ex);
+        rec[5 + 2 * c] = fdot2(gx, jy, ge, ey);
       }
       // 1/rho and sound speed at the vertex, for the wave speeds beta of the OE (+inf for rho <= 0)
       Real ri = Real(0), cs = Real(INFINITY);
       if (gt0(val4[0])) {
         ri = Real(1) / val4[0];
-        Real p = gm1 * (val4[3] - Real(0.5) * (val4[1] * val4[1] + val4[2] * val4[2]) * ri);
+        Real p = gm1 * (val4[3] - Real(0.5) * fdot2(val4[1], val4[1], val4[2], val4[2]) * ri);
         p = gt0(p) ? p : Real(0);
         cs = sqrt(gamma * p * ri);
       }
@@ -321,13 +321,13 @@ __device__ __forceinline__ void rk_tile(const MeshDev &m, const Phys &ph, StateD
       // physical second derivatives from the reference ones: the factors of
       // J^-T H J^-1, shared by the four components
       const Real gxx0 = jx * jx, gxe0 = Real(2) * jx * ex, gee0 = ex * ex;
-      const Real gxx1 = jx * jy, gxe1 = jx * ey + jy * ex, gee1 = ex * ey;
+      const Real gxx1 = jx * jy, gxe1 = fdot2(jx, ey, jy, ex), gee1 = ex * ey;
       const Real gxx2 = jy * jy, gxe2 = Real(2) * jy * ey, gee2 = ey * ey;
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        ho[3 * c + 0] = hxx[c] * gxx0 + hxe[c] * gxe0 + hee[c] * gee0;
-        ho[3 * c + 1] = hxx[c] * gxx1 + hxe[c] * gxe1 + hee[c] * gee1;
-        ho[3 * c + 2] = hxx[c] * gxx2 + hxe[c] * gxe2 + hee[c] * gee2;
+        ho[3 * c + 0] = fma(hxx[c], gxx0, fdot2(hxe[c], gxe0, hee[c], gee0));
+        ho[3 * c + 1] = fma(hxx[c], gxx1, fdot2(hxe[c], gxe1, hee[c], gee1));
+        ho[3 * c + 2] = fma(hxx[c], gxx2, fdot2(hxe[c], gxe2, hee[c], gee2));
       }
       vstore<12>(hso + Kc * 12, ho);   // 16-byte vector stores
     }
@@ -367,7 +367,7 @@ __device__ __forceinline__ void stats_tile(const MeshDev &m, StateDev<Real> uh, 
       Real u[4];
       eval_fixed<Real, NB>(off, hi, vol_xi(NV, mu), vol_eta(NV, mu), u);
       dr[0] = max_nn(dr[0], fabs(u[0]));
-      dr[1] = max_nn(dr[1], u[1] * u[1] + u[2] * u[2]);   // squared: one square root per cell below
+      dr[1] = max_nn(dr[1], fdot2(u[1], u[1], u[2], u[2]));   // squared: one square root per cell below
       dr[2] = max_nn(dr[2], fabs(u[3]));
       dr[3] = max_nn(dr[3], fabs(u[1]));
       dr[4] = max_nn(dr[4], fabs(u[2]));
@@ -396,31 +396,31 @@ __device__ __forceinline__ void ghost_vertex(int tag, const Real val[4], const R
     for (int c = 0; c < 4; ++c) {
       const Real hxx = hes[3 * c], hxy = hes[3 * c + 1], hyy = hes[3 * c + 2];
       // (R H R)_ab with R symmetric
-      const Real a0 = R00 * hxx + R01 * hxy, a1 = R00 * hxy + R01 * hyy;   // row 0 of R H
-      const Real b0 = R01 * hxx + R11 * hxy, b1 = R01 * hxy + R11 * hyy;   // row 1 of R H
-      RHR[c][0] = a0 * R00 + a1 * R01;
-      RHR[c][1] = a0 * R01 + a1 * R11;
-      RHR[c][2] = b0 * R01 + b1 * R11;
+      const Real a0 = fdot2(R00, hxx, R01, hxy), a1 = fdot2(R00, hxy, R01, hyy);   // row 0 of R H
+      const Real b0 = fdot2(R01, hxx, R11, hxy), b1 = fdot2(R01, hxy, R11, hyy);   // row 1 of R H
+      RHR[c][0] = fdot2(a0, R00, a1, R01);
+      RHR[c][1] = fdot2(a0, R01, a1, R11);
+      RHR[c][2] = fdot2(b0, R01, b1, R11);
     }
 #pragma unroll
     for (int c = 0; c < 4; c += 3) {
       ov[c] = val[c];
-      og[2 * c] = R00 * grd[2 * c] + R01 * grd[2 * c + 1];
-      og[2 * c + 1] = R01 * grd[2 * c] + R11 * grd[2 * c + 1];
+      og[2 * c] = fdot2(R00, grd[2 * c], R01, grd[2 * c + 1]);
+      og[2 * c + 1] = fdot2(R01, grd[2 * c], R11, grd[2 * c + 1]);
       oh[3 * c] = RHR[c][0]; oh[3 * c + 1] = RHR[c][1]; oh[3 * c + 2] = RHR[c][2];
     }
-    ov[1] = R00 * val[1] + R01 * val[2];
-    ov[2] = R01 * val[1] + R11 * val[2];
+    ov[1] = fdot2(R00, val[1], R01, val[2]);
+    ov[2] = fdot2(R01, val[1], R11, val[2]);
     // gradient matrix G[a][b] = d m_a / d x_b -> R G R
     const Real G00 = grd[2], G01 = grd[3], G10 = grd[4], G11 = grd[5];
-    const Real A00 = R00 * G00 + R01 * G10, A01 = R00 * G01 + R01 * G11;
-    const Real A10 = R01 * G00 + R11 * G10, A11 = R01 * G01 + R11 * G11;
-    og[2] = A00 * R00 + A01 * R01; og[3] = A00 * R01 + A01 * R11;
-    og[4] = A10 * R00 + A11 * R01; og[5] = A10 * R01 + A11 * R11;
+    const Real A00 = fdot2(R00, G00, R01, G10), A01 = fdot2(R00, G01, R01, G11);
+    const Real A10 = fdot2(R01, G00, R11, G10), A11 = fdot2(R01, G01, R11, G11);
+    og[2] = fdot2(A00, R00, A01, R01); og[3] = fdot2(A00, R01, A01, R11);
+    og[4] = fdot2(A10, R00, A11, R01); og[5] = fdot2(A10, R01, A11, R11);
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
-      oh[3 + r] = R00 * RHR[1][r] + R01 * RHR[2][r];
-      oh[6 + r] = R01 * RHR[1][r] + R11 * RHR[2][r];
+      oh[3 + r] = fdot2(R00, RHR[1][r], R01, RHR[2][r]);
+      oh[6 + r] = fdot2(R01, RHR[1][r], R11, RHR[2][r]);
     }
   } else if (tag >= 3) {   // constant exterior state: no derivatives
     Real st[4];
@@ -493,7 +493,7 @@ __device__ __forceinline__ void edge_tile(const MeshDev &m, const Phys &ph, cons
       for (int c = 0; c < 4; ++c) val[c] = rec[c];
 #pragma unroll
       for (int q = 0; q < 8; ++q) grd[q] = rec[4 + q];
-      const Real r_own = fabs(val[1] * nx + val[2] * ny) * rec[12] + rec[13];
+      const Real r_own = fma(fabs(fdot2(val[1], nx, val[2], ny)), rec[12], rec[13]);
       Real r_oth;
       if (cn >= 0) {
         const int xvtx = (jn + 2 - ev) % 3;            // the neighbour's copy of this vertex
@@ -505,7 +505,7 @@ __device__ __forceinline__ void edge_tile(const MeshDev &m, const Phys &ph, cons
         for (int q = 0; q < 8; ++q) xg[q] = xr[4 + q];
 #pragma unroll
         for (int q = 0; q < 12; ++q) xh[q] = hot[q];
-        r_oth = fabs(xv[1] * nx + xv[2] * ny) * xr[12] + xr[13];
+        r_oth = fma(fabs(fdot2(xv[1], nx, xv[2], ny)), xr[12], xr[13]);
       } else {
         double px = 0.0, py = 0.0;
         if (cn == -7) { px = m.vxy[(2 * ov) * nt + Kc]; py = m.vxy[(2 * ov + 1) * nt + Kc]; }
@@ -528,17 +528,17 @@ __device__ __forceinline__ void edge_tile(const MeshDev &m, const Phys &ph, cons
       }
       if (!cw) {   // rotate the momentum jumps to (m_n, m_t) with the owner's normal
         Real t0 = jv[1], t1 = jv[2];
-        jv[1] = t0 * nx + t1 * ny; jv[2] = -t0 * ny + t1 * nx;
+        jv[1] = fdot2(t0, nx, t1, ny); jv[2] = fdot2(t1, nx, -t0, ny);
 #pragma unroll
         for (int d = 0; d < 2; ++d) {
           t0 = jg[1][d]; t1 = jg[2][d];
-          jg[1][d] = t0 * nx + t1 * ny; jg[2][d] = -t0 * ny + t1 * nx;
+          jg[1][d] = fdot2(t0, nx, t1, ny); jg[2][d] = fdot2(t1, nx, -t0, ny);
         }
         if (hess) {
 #pragma unroll
           for (int r = 0; r < 3; ++r) {
             t0 = jh[1][r]; t1 = jh[2][r];
-            jh[1][r] = t0 * nx + t1 * ny; jh[2][r] = -t0 * ny + t1 * nx;
+            jh[1][r] = fdot2(t0, nx, t1, ny); jh[2][r] = fdot2(t1, nx, -t0, ny);
           }
         }
       }
@@ -646,11 +646,11 @@ __device__ __noinline__ void limit_mixed_fp64(const MeshDev &m, const Phys &ph, 
 #pragma unroll
     for (int p = 0; p < NE + 2; ++p) {
       const double w0 = a0[0] + th1 * d[p][0], w1 = a0[1] + d[p][1], w2 = a0[2] + d[p][2], w3 = a0[3] + d[p][3];
-      const double q = w1 * w1 + w2 * w2;
+      const double q = fdot2(w1, w1, w2, w2);
       vmax2 = fmax(vmax2, q / (w0 * w0));
       emin = fmin(emin, w3 - 0.5 * q / w0);
     }
-    const double RE = r22 * (Sa[3] + sqrt(vmax2) * (Sa[1] + Sa[2]) + vmax2 * th1 * Sa[0]);
+    const double RE = r22 * fma(sqrt(vmax2), Sa[1] + Sa[2], fma(vmax2 * th1, Sa[0], Sa[3]));
     const double eps2 = fmin(Ebar, 1e-13);
     const double tgt2 = fmin(Ebar, eps2 + 2.0 * RE);
     const double th2 = emin < tgt2 ? (Ebar - tgt2) / (Ebar - emin) : 1.0;
@@ -782,8 +782,8 @@ __device__ __forceinline__ void limit_and_trace_mixed(const MeshDev &m, const Ph
   bool avg_ok;
   float eps1, eps2;
   {
-    const float q2 = a0f[1] * a0f[1] + a0f[2] * a0f[2], pe = a0f[3] * a0f[0];
-    if (a0f[0] > 2e-13f && pe - 0.5f * q2 > 2e-13f * a0f[0] + 1e-5f * (fabsf(pe) + 0.5f * q2)) {
+    const float q2 = fdot2(a0f[1], a0f[1], a0f[2], a0f[2]), pe = a0f[3] * a0f[0];
+    if (a0f[0] > 2e-13f && fmaf(-0.5f, q2, pe) > fdot2(2e-13f, a0f[0], 1e-5f, fmaf(0.5f, q2, fabsf(pe)))) {
       avg_ok = true;
       eps1 = eps2 = float(1e-13);
     } else {
@@ -810,9 +810,9 @@ __device__ __forceinline__ void limit_and_trace_mixed(const MeshDev &m, const Ph
         if (!(r >= eps1 + 1e-5f * S[0])) return false;
         const float m1 = a0f[1] + d[1], m2 = a0f[2] + d[2], E = a0f[3] + d[3];
         const float ri = 1.0f / r;
-        const float q = (m1 * m1 + m2 * m2) * ri;           // |m|^2 / rho
+        const float q = fdot2(m1, m1, m2, m2) * ri;          // |m|^2 / rho
         const float v = sqrtf(q * ri);                       // |v|
-        const float margin = 1e-5f * (S[3] + v * (S[1] + S[2]) + v * v * S[0]) + 1e-6f * (fabsf(E) + q);
+        const float margin = fdot2(1e-5f, fmaf(v, S[1] + S[2], fmaf(v * v, S[0], S[3])), 1e-6f, fabsf(E) + q);
         return E - 0.5f * q >= eps2 + margin;
       };
       bool ok = true;
@@ -1066,7 +1066,7 @@ __device__ __forceinline__ void oe_bp_tile(const MeshDev &m, const Phys &ph, Sta
           for (int p = 0; p < NE + 2; ++p) {
             const double w0 = a0[0] + th1 * dev[p][0], w1 = a0[1] + dev[p][1], w2 = a0[2] + dev[p][2],
                          w3 = a0[3] + dev[p][3];
-            const double q = 0.5 * (w1 * w1 + w2 * w2);
+            const double q = 0.5 * fdot2(w1, w1, w2, w2);
             if (!(w0 > 0.0) || w3 * w0 - q < eps2 * w0) emin = fmin(emin, w3 - q / w0);
           }
           double th2 = 1.0;
