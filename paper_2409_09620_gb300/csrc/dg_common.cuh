@@ -285,8 +285,7 @@ __device__ __forceinline__ bool nonzero_bits(float x) { return (__float_as_int(x
 
 // F(u) . n and the spectral radius |v.n| + c (+inf for rho <= 0) with one reciprocal
 template <typename T>
-__device__ __forceinline__ T flux_speed(const T u[4], T nx, T ny, T gm1, T gamma, T f[4]) {
-  const T ri = T(1) / u[0];
+__device__ __forceinline__ T flux_speed_ri(const T u[4], T ri, T nx, T ny, T gm1, T gamma, T f[4]) {
   const T p = gm1 * (u[3] - T(0.5) * fdot2(u[1], u[1], u[2], u[2]) * ri);
   const T mn = fdot2(u[1], nx, u[2], ny);
   const T vn = mn * ri;
@@ -297,6 +296,39 @@ __device__ __forceinline__ T flux_speed(const T u[4], T nx, T ny, T gm1, T gamma
   if (!gt0(u[0])) return T(INFINITY);
   const T pc = gt0(p) ? p : T(0);
   return fabs(vn) + sqrt(gamma * pc * ri);
+}
+template <typename T>
+__device__ __forceinline__ T flux_speed(const T u[4], T nx, T ny, T gm1, T gamma, T f[4]) {
+  return flux_speed_ri(u, T(1) / u[0], nx, ny, gm1, gamma, f);
+}
+
+// 1 / x[p] for n values from one division (Montgomery's batch inversion:
+// prefix products, one reciprocal, back-substitution with two multiplies
+// per value; a few ulps).  If a prefix product is not a normal number (a
+// zero, a non-finite or an extreme value) every value is divided instead.
+template <int n>
+__device__ __forceinline__ void batch_reciprocal(const double x[n], double r[n]) {
+  double c[n];
+  c[0] = x[0];
+  unsigned bad = 0;
+#pragma unroll
+  for (int p = 0; p < n; ++p) {
+    if (p > 0) c[p] = c[p - 1] * x[p];
+    const unsigned ex = unsigned(__double_as_longlong(c[p]) >> 52) & 0x7ffu;
+    bad |= (ex == 0u) | (ex == 0x7ffu);
+  }
+  if (bad) {
+#pragma unroll
+    for (int p = 0; p < n; ++p) r[p] = 1.0 / x[p];
+    return;
+  }
+  double inv = 1.0 / c[n - 1];
+#pragma unroll
+  for (int p = n - 1; p > 0; --p) {
+    r[p] = inv * c[p - 1];
+    inv = inv * x[p];
+  }
+  r[0] = inv;
 }
 
 // spectral radius |v.n| + c; +inf for rho <= 0, pressure clamped at 0

@@ -1093,8 +1093,13 @@ __device__ __forceinline__ void oe_bp_tile(const MeshDev &m, const Phys &ph, Sta
   #pragma unroll
           for (int l = 1; l < NB; ++l) out.hi[(c * (NB - 1) + (l - 1)) * nt + Kc] = hi[c][l];
       }
-      // traces, F.n and wave speed of the limited state at the edge Gauss points
+      // traces, F.n and wave speed of the limited state at the edge Gauss points,
+      // with the reciprocal densities of all points from one division
       const Real gm1 = phys_gm1<Real>(ph);
+      double rho_t[NE], ri_t[NE];
+  #pragma unroll
+      for (int p = 0; p < NE; ++p) rho_t[p] = a0[0] + th_r * dev[p][0];
+      batch_reciprocal<NE>(rho_t, ri_t);
   #pragma unroll
       for (int i = 0; i < 3; ++i) {
   #pragma unroll
@@ -1102,7 +1107,7 @@ __device__ __forceinline__ void oe_bp_tile(const MeshDev &m, const Phys &ph, Sta
           Real u[4], f[4];
   #pragma unroll
           for (int c = 0; c < 4; ++c) u[c] = Real(a0[c] + (c == 0 ? th_r : th_a) * dev[i * NQ + nu][c]);
-          amax = max_nn(amax, double(flux_speed(u, nxs[i], nys[i], gm1, gamma, f)));
+          amax = max_nn(amax, double(flux_speed_ri(u, ri_t[i * NQ + nu], nxs[i], nys[i], gm1, gamma, f)));
           Real o8[8];
   #pragma unroll
           for (int q = 0; q < 4; ++q) { o8[q] = u[q]; o8[4 + q] = f[q]; }
