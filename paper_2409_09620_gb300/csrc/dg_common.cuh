@@ -304,7 +304,7 @@ __device__ __forceinline__ T flux_speed(const T u[4], T nx, T ny, T gm1, T gamma
 
 // 1 / x[p] for n values from one division (Montgomery's batch inversion:
 // prefix products, one reciprocal, back-substitution with two multiplies
-// per value; a few ulps).  If a prefix product is not a normal number (a
+// per value; each result within about 2n roundings of 1 / x[p]).  If a prefix product is not a normal number (a
 // zero, a non-finite or an extreme value) every value is divided instead.
 template <int n>
 __device__ __forceinline__ void batch_reciprocal(const double x[n], double r[n]) {
