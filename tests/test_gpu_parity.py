@@ -185,6 +185,30 @@ def test_alpha(oracle_mod, N, k, case):
 
 
 @pytest.mark.parametrize("k", [1, 2])
+def test_alpha_extreme_densities(oracle_mod, N, k):
+    """Cells whose states are scaled by 1e-160 and 1e+150 (velocity and sound
+    speed unchanged): the product of a cell's trace densities leaves the
+    normal range, so the kernel takes one division per point instead of the
+    batch reciprocal.  alpha still matches the oracle."""
+    O = oracle_mod
+    wl = _cases()["riemann"](k)
+    om, u0, mesh, solver = _setup(O, N, wl)
+    cf = O.config_for(wl)
+    u = _perturbed(u0, 8, amp=0.01)
+    u[:, :, 3] *= 1e-160
+    u[:, :, 40] *= 1e150
+    np.testing.assert_allclose(solver.op_alpha(u, 0.0), om.alpha(cf, u, 0.0), rtol=1e-13)
+    # the scaled cells in a slow quiescent gas (rho 1, p 0.01): they set alpha
+    w = np.zeros_like(u)
+    w[0, 0] = 1.0
+    w[3, 0] = 0.01 / 0.4
+    w[:, :, [3, 40]] = u[:, :, [3, 40]]
+    a = solver.op_alpha(w, 0.0)
+    np.testing.assert_allclose(a, om.alpha(cf, w, 0.0), rtol=1e-13)
+    assert a > 0.5
+
+
+@pytest.mark.parametrize("k", [1, 2])
 @pytest.mark.parametrize("case", ["vortex", "sedov", "riemann", "dmr"])
 def test_one_step(oracle_mod, N, k, case):
     """All rows: one SSP-RK3 step of the graph-captured solver vs the oracle."""
