@@ -47,16 +47,17 @@ UNIT = "cell-stage updates/s"
 # u_n term), vertex records 269, Hessians 73, block sums 6.  k_stats:
 # deviations at the volume points 231, edge OE records 187 per edge x 1.5.
 # k_oe_bp: sigma 87, damping 38, limiter at the 11 points 497, traces and
-# wave speeds 297.
-ALGO_FLOPS_P2 = {"rk": 1745.0, "stats": 512.0, "oe_bp": 919.0}
+# wave speeds 313 (the nine reciprocal densities from one division and 24
+# multiplies).
+ALGO_FLOPS_P2 = {"rk": 1745.0, "stats": 512.0, "oe_bp": 935.0}
 # FP64 flops per cell-stage the hardware executed for the same kernels
 # (2 DFMA + DMUL + DADD from ncu captures / cells; k_rk: mean of its three
-# stages 1891 / 1963 / 1963); division, square root and exp expand into
+# stages 1893 / 1965 / 1965); division, square root and exp expand into
 # DFMA sequences.  None = not re-measured since the kernel last changed.
-EXECUTED_FLOPS_P2 = {"rk": 1939.0, "stats": 737.0, "oe_bp": 1228.0}
+EXECUTED_FLOPS_P2 = {"rk": 1941.0, "stats": 739.0, "oe_bp": 1175.0}
 # DRAM bytes (read + write) per launch from the same captures (k_rk: mean of
-# its stages 1.595 / 1.804 / 1.805 GB).
-TRAFFIC_PER_LAUNCH = {"rk": 1.735e9, "stats": 0.947e9, "oe_bp": 1.371e9}
+# its stages 1.596 / 1.807 / 1.807 GB).
+TRAFFIC_PER_LAUNCH = {"rk": 1.737e9, "stats": 0.947e9, "oe_bp": 1.376e9}
 # Mixed form (P2, FP32 modes and geometry, FP64 averages): algorithmic HBM
 # bytes per cell-stage, each array element moved once and neighbour data
 # taken from L2.  k_rk: u_n, v and u_h (3 x 112), geometry 80, own traces 144,
@@ -66,7 +67,7 @@ TRAFFIC_PER_LAUNCH = {"rk": 1.735e9, "stats": 0.947e9, "oe_bp": 1.371e9}
 # records 1.5 x 64, internal nodes 16, output state 112, traces 144.
 ALGO_BYTES_MIXED_P2 = {"rk": 800.0, "stats": 474.0, "oe_bp": 552.0}
 # DRAM bytes per launch of the mixed-form kernels from one ncu capture
-TRAFFIC_MIXED_PER_LAUNCH = {"rk": 0.712e9, "stats": 0.495e9, "oe_bp": 0.554e9}
+TRAFFIC_MIXED_PER_LAUNCH = {"rk": 0.713e9, "stats": 0.495e9, "oe_bp": 0.554e9}
 
 
 def load_peaks():
