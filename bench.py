@@ -251,6 +251,9 @@ def main():
     ap.add_argument("--no-paper-meshes", action="store_true",
                     help="skip the forward-facing-step and wedge meshes")
     ap.add_argument("--no-scalar", action="store_true", help="skip the scalar conservation laws")
+    ap.add_argument("--to-t-end", type=float, default=0.0,
+                    help="also run the main workload to this end time in the mixed form and in FP64 "
+                         "(off by default: the FP64 run to t = 0.2 takes about 11 minutes)")
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-rate", type=float, default=30.0)
     args = ap.parse_args()
@@ -474,6 +477,29 @@ def main():
                                  "min_cfl_area_ratio": m_g.min_cfl_area(k, 0) / m_g.min_cfl_area(k, 1)}
         cfl_gain["paper_dmr_mean_dt_ratio"] = {"P1": 2.869570, "P2": 4.486689}
 
+    # the whole problem to an end time in both forms: steps, counters, wall
+    # time and the density L1 difference of the mixed form from FP64
+    to_t_end = None
+    if args.to_t_end > 0.0:
+        to_t_end = {"t_end": args.to_t_end}
+        res = {}
+        for label, prec in (("mixed", N.PREC_MIXED), ("fp64", N.PREC_FP64)):
+            sv = N.Solver(mesh, N.config_for(wl, precision=prec), u0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st_e, _ = sv.advance(args.to_t_end)
+            el = time.perf_counter() - t0
+            res[label] = sv.get_state()[0]
+            to_t_end[label] = {"steps": st_e["steps"], "t": st_e["t"], "seconds": el,
+                               "limited_cells": st_e["limited_cells"], "nonphysical": st_e["nonphysical"],
+                               "cfl_breaches": st_e["cfl_breaches"],
+                               "cell_stages_per_s": nt * 3 * st_e["steps"] / el}
+            del sv
+        area = mesh.geometry(wl.k)["area"]
+        ra, rb = res["mixed"][0, 0], res["fp64"][0, 0]
+        to_t_end["density_l1_rel_mixed_vs_fp64"] = float((np.abs(ra - rb) * area).sum() / (np.abs(rb) * area).sum())
+        to_t_end["density_min"] = {"mixed": float(ra.min()), "fp64": float(rb.min())}
+
     # the paper's own domains (Sec. 5) on near-equilateral lattice meshes of
     # about its cell counts: throughput, and the mean BP time step of the
     # optimal over the classical decomposition over the first steps
@@ -601,6 +627,7 @@ def main():
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": 19 * args.steps, "clocks": clocks, "fp32": mixed, "batch": batch,
                 "serving": serving, "bp_cfl_gain": cfl_gain, "paper_meshes": paper_meshes, "scalar": scalar,
+                "to_t_end": to_t_end,
                 "peaks": {"source": peak_src, "hbm_gbs": peaks.get("hbm_gbs")},
                 "stats": {"limited_cells": st["limited_cells"], "cfl_breaches": st["cfl_breaches"],
                           "t": st["t"], "dt_last": st["dt_last"]}}
