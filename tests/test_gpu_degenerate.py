@@ -1,7 +1,8 @@
 """GPU parity on degenerate and boundary-sized meshes: one cell with walls on
 every edge, two cells, an 18-cell periodic grid (a cell meets the same
 neighbour across a periodic and an interior edge), 8 cells with walls, the
-double Mach reflection on 8 cells (every boundary kind), exactly one tile of
+double Mach reflection on 8 cells (walls, inflow and pre-shock states, the
+moving shock), exactly one tile of
 128 cells, and one tile plus a ragged tail of 4.  One SSP-RK3 step <= 1e-12 and ten steps <= 1e-9
 against the oracle in FP64 (counters bit-exact); the mixed form on the same
 meshes keeps every cell average admissible."""
