@@ -513,15 +513,21 @@ static double cell_alpha(const or_mesh *m, const or_config *cf, const double *u,
   return best;
 }
 
-double or_alpha(const or_mesh *m, const or_config *cf, const double *u, double t) {
-  double *a = malloc(sizeof(double) * m->nt);
+double or_alpha_cells(const or_mesh *m, const or_config *cf, const double *u, double t,
+                      const int64_t *cells, int64_t ncells) {
+  int64_t n = cells ? ncells : m->nt;
+  double *a = malloc(sizeof(double) * (n > 0 ? n : 1));
 #pragma omp parallel for schedule(static)
-  for (int64_t K = 0; K < m->nt; ++K) a[K] = cell_alpha(m, cf, u, K, t);
+  for (int64_t j = 0; j < n; ++j) a[j] = cell_alpha(m, cf, u, cells ? cells[j] : j, t);
   double best = 0.0;
-  for (int64_t K = 0; K < m->nt; ++K)
-    if (a[K] > best || a[K] != a[K]) best = a[K];
+  for (int64_t j = 0; j < n; ++j)
+    if (a[j] > best || a[j] != a[j]) best = a[j];
   free(a);
   return best;
+}
+
+double or_alpha(const or_mesh *m, const or_config *cf, const double *u, double t) {
+  return or_alpha_cells(m, cf, u, t, NULL, 0);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -618,8 +624,10 @@ int or_rk_stage(const or_mesh *m, const or_config *cf, const double *un, const d
 /* Global statistics of the OE procedure (eqs. OEScalar:Coef2, normOmg,      */
 /* RIOESys:Coef1): domain means and sup deviations at the volume points      */
 /* ------------------------------------------------------------------------ */
-int or_stats(const or_mesh *m, const or_config *cf, const double *u, double *stats) {
+int or_stats_cells(const or_mesh *m, const or_config *cf, const double *u, const int64_t *cells,
+                   int64_t ncells, double *stats) {
   int k = cf->k, nb = nbasis(k);
+  int64_t n = cells ? ncells : m->nt;
   double sum[4] = {0, 0, 0, 0}, omega = 0.0;
   for (int64_t K = 0; K < m->nt; ++K) {
     cellgeo g;
@@ -629,9 +637,10 @@ int or_stats(const or_mesh *m, const or_config *cf, const double *u, double *sta
   }
   double mean[4];
   for (int c = 0; c < 4; ++c) mean[c] = sum[c] / omega;
-  double *dev = malloc(sizeof(double) * 5 * m->nt);
+  double *dev = malloc(sizeof(double) * 5 * (n > 0 ? n : 1));
 #pragma omp parallel for schedule(static)
-  for (int64_t K = 0; K < m->nt; ++K) {
+  for (int64_t j = 0; j < n; ++j) {
+    const int64_t K = cells ? cells[j] : j;
     cellgeo g;
     cell_geo(m, K, &g);
     const double (*B)[3];
@@ -652,12 +661,12 @@ int or_stats(const or_mesh *m, const or_config *cf, const double *u, double *sta
       if (d1 > d[3]) d[3] = d1;
       if (d2 > d[4]) d[4] = d2;
     }
-    for (int q = 0; q < 5; ++q) dev[5 * K + q] = d[q];
+    for (int q = 0; q < 5; ++q) dev[5 * j + q] = d[q];
   }
   double D[5] = {0, 0, 0, 0, 0};
-  for (int64_t K = 0; K < m->nt; ++K)
+  for (int64_t j = 0; j < n; ++j)
     for (int q = 0; q < 5; ++q)
-      if (dev[5 * K + q] > D[q]) D[q] = dev[5 * K + q];
+      if (dev[5 * j + q] > D[q]) D[q] = dev[5 * j + q];
   free(dev);
   for (int c = 0; c < 4; ++c) stats[c] = mean[c];
   stats[4] = D[0];
@@ -667,6 +676,10 @@ int or_stats(const or_mesh *m, const or_config *cf, const double *u, double *sta
   stats[8] = D[3];
   stats[9] = D[4];
   return OR_OK;
+}
+
+int or_stats(const or_mesh *m, const or_config *cf, const double *u, double *stats) {
+  return or_stats_cells(m, cf, u, NULL, 0, stats);
 }
 
 /* ------------------------------------------------------------------------ */

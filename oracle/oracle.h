@@ -82,6 +82,10 @@ void or_eval(const or_mesh *m, int k, const double *u, int64_t K, double x, doub
 
 /* alpha: max wave speed over edge Gauss points (eq. 1250) */
 double or_alpha(const or_mesh *m, const or_config *cf, const double *u, double t);
+/* the same maximum over a subset of the cells (cells == NULL: all); it reads
+ * only those cells' own coefficients */
+double or_alpha_cells(const or_mesh *m, const or_config *cf, const double *u, double t,
+                      const int64_t *cells, int64_t ncells);
 /* DG operator L(u) (eq. DGSystem:Dis); cells == NULL means all cells */
 int or_L(const or_mesh *m, const or_config *cf, const double *u, double alpha, double t,
          double *L, const int64_t *cells, int64_t ncells);
@@ -93,6 +97,11 @@ int or_rk_stage(const or_mesh *m, const or_config *cf, const double *un, const d
  * deviations of rho, |m - mean m| and E at the volume points, stats[7] =
  * |Omega|, stats[8..9] = sup deviations of m1 and m2 (component-wise OE) */
 int or_stats(const or_mesh *m, const or_config *cf, const double *u, double *stats);
+/* the same with the sup deviations taken over a subset of the cells (cells ==
+ * NULL: all); the domain means still sum the cell averages (mode 0) of every
+ * cell, in cell order, so only mode 0 of the other cells is read */
+int or_stats_cells(const or_mesh *m, const or_config *cf, const double *u, const int64_t *cells,
+                   int64_t ncells, double *stats);
 /* OE procedure F_tau; sigma (nullable) receives sigma[(c * 3 + j) * nt + K] */
 int or_oe(const or_mesh *m, const or_config *cf, const double *u, double dt,
           const double *stats, double t, double *out, double *sigma,

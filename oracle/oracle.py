@@ -76,9 +76,11 @@ def lib():
         L.or_project.argtypes = [P, C.c_int, P, P]
         L.or_eval.argtypes = [P, C.c_int, P, i64, dbl, dbl, P]
         L.or_alpha.argtypes = [P, P, P, dbl]; L.or_alpha.restype = dbl
+        L.or_alpha_cells.argtypes = [P, P, P, dbl, P, i64]; L.or_alpha_cells.restype = dbl
         L.or_L.argtypes = [P, P, P, dbl, dbl, P, P, i64]
         L.or_rk_stage.argtypes = [P, P, P, P, dbl, dbl, dbl, dbl, dbl, P, P, i64]
         L.or_stats.argtypes = [P, P, P, P]
+        L.or_stats_cells.argtypes = [P, P, P, P, i64, P]
         L.or_oe.argtypes = [P, P, P, dbl, P, dbl, P, P, P, i64]
         L.or_limit.argtypes = [P, P, P, P, P, P, i64]
         L.or_point_minima.argtypes = [P, P, P, P]
@@ -207,8 +209,12 @@ class OracleMesh:
         return out
 
     # -- stage operators --------------------------------------------------
-    def alpha(self, cf, u, t=0.0):
-        return lib().or_alpha(self.h, C.byref(cf), _p(np.ascontiguousarray(u)), t)
+    def alpha(self, cf, u, t=0.0, cells=None):
+        u = np.ascontiguousarray(u)
+        if cells is None:
+            return lib().or_alpha(self.h, C.byref(cf), _p(u), t)
+        cl = np.ascontiguousarray(cells, dtype=np.int64)
+        return lib().or_alpha_cells(self.h, C.byref(cf), _p(u), t, _p(cl), cl.size)
 
     def L(self, cf, u, alpha, t=0.0, cells=None):
         u = np.ascontiguousarray(u)
@@ -225,9 +231,14 @@ class OracleMesh:
                           0 if cl is None else cl.size)
         return out
 
-    def stats(self, cf, u):
+    def stats(self, cf, u, cells=None):
         st = np.empty(10)
-        lib().or_stats(self.h, C.byref(cf), _p(np.ascontiguousarray(u)), _p(st))
+        u = np.ascontiguousarray(u)
+        if cells is None:
+            lib().or_stats(self.h, C.byref(cf), _p(u), _p(st))
+        else:
+            cl = np.ascontiguousarray(cells, dtype=np.int64)
+            lib().or_stats_cells(self.h, C.byref(cf), _p(u), _p(cl), cl.size, _p(st))
         return st
 
     def oe(self, cf, u, dt, stats=None, t=0.0, cells=None, want_sigma=False):

@@ -570,7 +570,7 @@ __device__ __forceinline__ bool take_ticket(unsigned *cnt, unsigned total) {
     const unsigned t = atomicAdd(cnt, 1u);
     const int last = t + 1 == total;
     if (last) {
-      atomicExch(cnt, 0u);               // every ticket is taken: reset for the next round
+      atomicExch(cnt, 0u);               // every ticket is taken: reset for the next launch
       __threadfence();
     }
     s_last = last;
