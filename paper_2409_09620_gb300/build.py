@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libdg_gb300.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["dg_kernels.cu", "dg_api.cu", "dg_noalloc.cu", "dg_batch.cu", "dg_serve.cu", "dg_scalar.cu"]
+SOURCES = ["dg_kernels.cu", "dg_api.cu", "dg_noalloc.cu", "dg_batch.cu", "dg_serve.cu", "dg_scalar.cu",
+           "dg_mesh_host.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
          "-I", os.path.join(ROOT, "include")]
@@ -42,7 +43,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     cc = nvcc()
 
     def compile_one(src):
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+        obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
         cmd = [cc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:

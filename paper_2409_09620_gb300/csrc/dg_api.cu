@@ -12,6 +12,7 @@
 
 #include "../../include/dg.h"
 #include "dg_internal.h"
+#include "dg_mesh_host.h"
 
 using namespace dg;
 
@@ -113,113 +114,27 @@ int32_t set_error(int32_t code, const char *msg) { return fail(code, "%s", msg);
 // ============================================================================
 // Mesh
 // ============================================================================
-namespace {
-struct EdgeKey {
-  int32_t lo, hi;
-  int64_t cell;
-  int32_t edge;
-};
-}  // namespace
-
 extern "C" int32_t dg_mesh_create(int64_t nv, const double *xy, int64_t nt, const int32_t *tri, const int32_t *canon,
                                   const int8_t *bc, dg_mesh **out) {
   if (!out) return fail(DG_EINVAL, "out is NULL");
   *out = nullptr;
-  if (nv <= 0 || nt <= 0 || !xy || !tri) return fail(DG_EINVAL, "empty mesh or NULL arrays (nv=%lld nt=%lld)",
-                                                       (long long)nv, (long long)nt);
-  if (nt >= (int64_t(1) << 29)) return fail(DG_EINVAL, "too many cells (%lld)", (long long)nt);
-  auto canon_of = [&](int32_t v) { return canon ? canon[v] : v; };
-  // validation: vertex ids, orientation
-  for (int64_t e = 0; e < 3 * nt; ++e)
-    if (tri[e] < 0 || tri[e] >= nv) return fail(DG_EMESH, "vertex id out of range at %lld", (long long)e);
-  if (canon)
-    for (int64_t v = 0; v < nv; ++v)
-      if (canon[v] < 0 || canon[v] >= nv) return fail(DG_EMESH, "canon id out of range at %lld", (long long)v);
-  for (int64_t K = 0; K < nt; ++K) {
-    const double *a = xy + 2 * tri[3 * K], *b = xy + 2 * tri[3 * K + 1], *c = xy + 2 * tri[3 * K + 2];
-    const double det = (b[0] - a[0]) * (c[1] - a[1]) - (c[0] - a[0]) * (b[1] - a[1]);
-    if (!(det > 0.0)) return fail(DG_EMESH, "cell %lld is not counter-clockwise with positive area", (long long)K);
-  }
-  // adjacency: sort edges by canonical vertex pair
-  std::vector<EdgeKey> keys((size_t)(3 * nt));
-  for (int64_t K = 0; K < nt; ++K)
-    for (int i = 0; i < 3; ++i) {
-      int32_t a = canon_of(tri[3 * K + (i + 1) % 3]), b = canon_of(tri[3 * K + (i + 2) % 3]);
-      if (a == b) return fail(DG_EMESH, "degenerate edge in cell %lld", (long long)K);
-      keys[3 * K + i] = {std::min(a, b), std::max(a, b), K, i};
-    }
-  std::sort(keys.begin(), keys.end(), [](const EdgeKey &x, const EdgeKey &y) {
-    if (x.lo != y.lo) return x.lo < y.lo;
-    if (x.hi != y.hi) return x.hi < y.hi;
-    if (x.cell != y.cell) return x.cell < y.cell;
-    return x.edge < y.edge;
-  });
+  HostMesh hm;
+  std::string msg;
+  const int32_t rc = build_host_mesh(nv, xy, nt, tri, canon, bc, TPB, hm, msg);
+  if (rc != DG_OK) return fail(rc, "%s", msg.c_str());
   auto m = new (std::nothrow) dg_mesh();
   if (!m) return fail(DG_ENOMEM, "host allocation failed");
   m->nv = nv;
   m->nt = nt;
-  m->nbr.assign((size_t)(3 * nt), -1);
-  m->nbr_edge.assign((size_t)(3 * nt), -1);
-  std::vector<int32_t> conn((size_t)(3 * nt));   // [3][nt]
-  for (size_t e = 0; e < keys.size();) {
-    size_t f = e + 1;
-    while (f < keys.size() && keys[f].lo == keys[e].lo && keys[f].hi == keys[e].hi) ++f;
-    if (f - e > 2) { delete m; return fail(DG_EMESH, "edge shared by more than two cells"); }
-    if (f - e == 2) {
-      const EdgeKey &p = keys[e], &q = keys[e + 1];
-      // the two cells must traverse the shared edge in opposite directions
-      int32_t pa = canon_of(tri[3 * p.cell + (p.edge + 1) % 3]);
-      int32_t qa = canon_of(tri[3 * q.cell + (q.edge + 1) % 3]);
-      if (pa == qa) { delete m; return fail(DG_EMESH, "edge traversed twice in the same direction"); }
-      m->nbr[3 * p.cell + p.edge] = (int32_t)q.cell;
-      m->nbr_edge[3 * p.cell + p.edge] = q.edge;
-      m->nbr[3 * q.cell + q.edge] = (int32_t)p.cell;
-      m->nbr_edge[3 * q.cell + q.edge] = p.edge;
-    } else {
-      const int8_t tag = bc ? bc[3 * keys[e].cell + keys[e].edge] : 0;
-      if (tag < DG_BC_REFLECT || tag > DG_BC_SHOCK) {
-        delete m;
-        return fail(DG_EMESH, "boundary edge %d of cell %lld has no valid tag", keys[e].edge, (long long)keys[e].cell);
-      }
-    }
-    e = f;
-  }
-  m->bnd_tag.assign((size_t)(3 * nt), 0);
-  for (int64_t K = 0; K < nt; ++K)
-    for (int i = 0; i < 3; ++i) {
-      const int32_t nbK = m->nbr[3 * K + i];
-      conn[(size_t)i * nt + K] = nbK >= 0 ? ((nbK << 2) | m->nbr_edge[3 * K + i]) : -(int32_t)bc[3 * K + i];
-      if (nbK < 0) m->bnd_tag[3 * K + i] = bc[3 * K + i];
-    }
-  // edge list: every edge once, owned by its lower cell id (or its only cell),
-  // ordered by owner; tiles of TPB cells own contiguous edge ranges
+  m->nbr = std::move(hm.nbr);
+  m->nbr_edge = std::move(hm.nbr_edge);
+  m->bnd_tag = std::move(hm.bnd_tag);
+  m->vxy_host = std::move(hm.vxy);
+  const std::vector<int32_t> &conn = hm.conn, &e_cell = hm.e_cell, &etile = hm.etile, &cedge = hm.cedge;
+  const std::vector<int8_t> &e_loc = hm.e_loc;
   const int64_t ntiles = num_blocks(nt);
-  std::vector<int32_t> e_cell, etile((size_t)ntiles + 1), cedge((size_t)(3 * nt));
-  std::vector<int8_t> e_loc;
-  for (int64_t K = 0; K < nt; ++K) {
-    if (K % TPB == 0) etile[(size_t)(K / TPB)] = (int32_t)e_cell.size();
-    for (int i = 0; i < 3; ++i) {
-      const int32_t nbK = m->nbr[3 * K + i];
-      if (nbK < 0 || K < nbK) {
-        cedge[(size_t)i * nt + K] = (int32_t)e_cell.size();
-        e_cell.push_back((int32_t)K);
-        e_loc.push_back((int8_t)i);
-      }
-    }
-  }
-  etile[(size_t)ntiles] = (int32_t)e_cell.size();
-  for (int64_t K = 0; K < nt; ++K)
-    for (int i = 0; i < 3; ++i) {
-      const int32_t nbK = m->nbr[3 * K + i];
-      if (nbK >= 0 && nbK < K) cedge[(size_t)i * nt + K] = cedge[(size_t)m->nbr_edge[3 * K + i] * nt + nbK];
-    }
+  if ((int64_t)etile.size() != ntiles + 1) { delete m; return fail(DG_EINVAL, "tile count mismatch"); }
   m->ne = (int64_t)e_cell.size();
-  m->vxy_host.resize((size_t)(6 * nt));
-  for (int64_t K = 0; K < nt; ++K)
-    for (int v = 0; v < 3; ++v) {
-      m->vxy_host[(size_t)(2 * v) * nt + K] = xy[2 * tri[3 * K + v]];
-      m->vxy_host[(size_t)(2 * v + 1) * nt + K] = xy[2 * tri[3 * K + v] + 1];
-    }
   double *part = nullptr, *mins = nullptr;
   cudaError_t e = cudaSuccess;
 #define MTRY(x)                                                                                         \

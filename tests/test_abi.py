@@ -33,3 +33,26 @@ def test_no_oracle_in_product():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in txt.lower() or f == "workloads.py", f
+
+
+def test_mesh_create_rejects_bad_input_before_any_device_call():
+    """dg_mesh_create validates on the host first: bad input returns its
+    status and a message without touching the device (so it runs here)."""
+    from paper_2409_09620_gb300 import build
+    lib = ctypes.CDLL(build.build())
+    lib.dg_mesh_create.restype = ctypes.c_int32
+    lib.dg_mesh_create.argtypes = [ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
+    lib.dg_last_error.restype = ctypes.c_char_p
+    xy = (ctypes.c_double * 6)(0, 0, 1, 0, 0, 1)
+    cw = (ctypes.c_int32 * 3)(0, 2, 1)
+    ccw = (ctypes.c_int32 * 3)(0, 1, 2)
+    walls = (ctypes.c_int8 * 3)(1, 1, 1)
+    out = ctypes.c_void_p(1)
+    assert lib.dg_mesh_create(3, xy, 1, ccw, None, walls, None) == -1              # DG_EINVAL: out NULL
+    assert lib.dg_mesh_create(3, xy, 0, ccw, None, walls, ctypes.byref(out)) == -1 and out.value is None
+    assert b"empty mesh" in lib.dg_last_error()
+    assert lib.dg_mesh_create(3, xy, 1, cw, None, walls, ctypes.byref(out)) == -2  # DG_EMESH
+    assert b"counter-clockwise" in lib.dg_last_error() and out.value is None
+    assert lib.dg_mesh_create(3, xy, 1, ccw, None, None, ctypes.byref(out)) == -2
+    assert b"no valid tag" in lib.dg_last_error()
