@@ -101,9 +101,13 @@ typedef struct dg_stats {
  * DG_BC_NONE).  Computes the neighbour of every edge on the host and the
  * per-cell geometry and optimal convex decomposition (eqs. 1040, 1139) on the
  * GPU.  Errors: DG_EINVAL (nt <= 0, nv <= 0, NULL arrays), DG_EMESH (vertex id
- * out of range, area <= 0, an edge shared by more than two cells or traversed
- * twice in the same direction, a boundary edge tagged DG_BC_NONE), DG_ENOMEM,
- * DG_ECUDA.  *out receives a handle owned by the caller (dg_mesh_destroy). */
+ * or canon id out of range, area <= 0, an edge whose canonical ends coincide,
+ * an edge shared by more than two cells or traversed twice in the same
+ * direction, two copies of a periodic edge that are not translates of each
+ * other (to 1e-9 relative), a boundary edge tagged DG_BC_NONE or out of
+ * range), DG_ENOMEM, DG_ECUDA.  These input checks run on the host before any
+ * device call.  *out receives a handle owned by the caller
+ * (dg_mesh_destroy). */
 int32_t dg_mesh_create(int64_t nv, const double *xy, int64_t nt, const int32_t *tri,
                        const int32_t *canon, const int8_t *bc, dg_mesh **out);
 void dg_mesh_destroy(dg_mesh *mesh);

@@ -2,6 +2,7 @@
 #include "dg_mesh_host.h"
 
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <new>
@@ -73,6 +74,16 @@ int32_t build(int64_t nv, const double *xy, int64_t nt, const int32_t *tri, cons
       int32_t pa = canon_of(tri[3 * p.cell + (p.edge + 1) % 3]);
       int32_t qa = canon_of(tri[3 * q.cell + (q.edge + 1) % 3]);
       if (pa == qa) return set_err(err, DG_EMESH, "edge traversed twice in the same direction");
+      // both ends of an identified (periodic) edge move by the same translation;
+      // for an ordinary interior edge both translations are zero
+      const int32_t p0 = tri[3 * p.cell + (p.edge + 1) % 3], p1 = tri[3 * p.cell + (p.edge + 2) % 3];
+      const int32_t q0 = tri[3 * q.cell + (q.edge + 1) % 3], q1 = tri[3 * q.cell + (q.edge + 2) % 3];
+      const double sx = xy[2 * q1] - xy[2 * p0], sy = xy[2 * q1 + 1] - xy[2 * p0 + 1];
+      const double tx = xy[2 * q0] - xy[2 * p1], ty = xy[2 * q0 + 1] - xy[2 * p1 + 1];
+      const double scale = 1.0 + std::fabs(sx) + std::fabs(sy);
+      if (!(std::fabs(sx - tx) <= 1e-9 * scale && std::fabs(sy - ty) <= 1e-9 * scale))
+        return set_err(err, DG_EMESH, "the two copies of periodic edge %d of cell %lld are not translates",
+                       p.edge, (long long)p.cell);
       hm.nbr[3 * p.cell + p.edge] = (int32_t)q.cell;
       hm.nbr_edge[3 * p.cell + p.edge] = q.edge;
       hm.nbr[3 * q.cell + q.edge] = (int32_t)p.cell;

@@ -25,7 +25,8 @@ struct HostMesh {
 // clockwise.  Returns 0 or DG_EINVAL (empty mesh, NULL arrays, too many
 // cells), DG_EMESH (vertex or canonical id out of range, area <= 0, an edge
 // with coincident canonical ends, an edge shared by more than two cells or
-// traversed twice in the same direction, a boundary edge without a valid tag)
+// traversed twice in the same direction, the two copies of a periodic edge
+// that are not translates of each other, a boundary edge without a valid tag)
 // or DG_ENOMEM, with a message in `err`.  `tile` is the number of cells per
 // tile of the edge list.
 int32_t build_host_mesh(int64_t nv, const double *xy, int64_t nt, const int32_t *tri, const int32_t *canon,

@@ -144,6 +144,16 @@ def test_host_builder_matches_oracle_adjacency(oracle_mod, driver, name, tile):
         assert np.array_equal(h["vxy"][2 * v + 1], mesh.xy[mesh.tri[:, v], 1])
 
 
+_STRIP_TRI = [[c, c + 1, c + 5] for c in range(3)] + [[c, c + 5, c + 4] for c in range(3)]
+_STRIP_CANON = np.array([0, 1, 2, 0, 4, 5, 6, 4], np.int32)
+
+
+def _strip(right_height):
+    xy = np.array([[i, 0.0] for i in range(4)] + [[i, 1.0] for i in range(4)])
+    xy[7, 1] = right_height
+    return xy
+
+
 def _bad_cases():
     """name -> (xy, tri, canon, bc, expected status, part of the message)"""
     sq = np.array([[0, 0], [1, 0], [1, 1], [0, 1], [-1, 0.5]], float)
@@ -163,6 +173,10 @@ def _bad_cases():
         "canon_degenerate_edge": (sq, [[0, 1, 2]], np.array([0, 0, 2, 3, 4], np.int32), w(1), DG_EMESH,
                                   "degenerate edge"),
         "empty": (np.zeros((0, 2)), np.zeros((0, 3), np.int32), None, None, DG_EINVAL, "empty mesh"),
+        # a 3 x 1 strip periodic in x; moving vertex 7 makes the right side
+        # 1.2 long against the left side's 1
+        "periodic_not_translates": (_strip(1.2), _STRIP_TRI, _STRIP_CANON, w(6), DG_EMESH, "not translates"),
+        "periodic_translates": (_strip(1.0), _STRIP_TRI, _STRIP_CANON, w(6), DG_OK, ""),
     }
 
 
