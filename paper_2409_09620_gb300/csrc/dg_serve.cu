@@ -9,7 +9,9 @@
 // waiting, so the GPU works while the caller submits new requests.  All
 // running solves advance together in the persistent batch kernel, each with
 // its own time step, so a result does not depend on which other solves ran
-// beside it.
+// beside it.  The queue, the budget and the retirement rules are the plain
+// C++ ServeScheduler (dg_serve_sched.cpp); this file is its device engine.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <deque>
@@ -18,6 +20,7 @@
 
 #include "../../include/dg.h"
 #include "dg_internal.h"
+#include "dg_serve_sched.h"
 
 namespace dg {
 struct BatchCore;
@@ -32,8 +35,9 @@ using namespace dg;
 
 namespace {
 
-struct Request {
-  int64_t id = 0;
+// what the device side keeps of a request: its inputs until it starts, its
+// mesh and solver while it runs, its result once done
+struct Payload {
   std::vector<double> xy;
   std::vector<int32_t> tri, canon;
   std::vector<int8_t> bc;
@@ -41,12 +45,8 @@ struct Request {
   std::vector<double> coeffs, result;
   double t_end = 0.0;
   int64_t nv = 0, nt = 0;
-  size_t bytes = 0;
-  int32_t state = DG_REQ_QUEUED, error = DG_OK;
   dg_mesh *mesh = nullptr;
   dg_solver *solver = nullptr;
-  double submit_s = 0.0, start_s = 0.0, done_s = 0.0, t = 0.0;
-  int64_t steps = 0;
 };
 
 // device bytes of one solve: mesh geometry and connectivity + solver buffers
@@ -60,32 +60,89 @@ size_t solve_bytes(int64_t nt, int k, int prec) {
   return (size_t)nt * (mesh + state + exch) + ((size_t)nt / 128 + 1) * part + 4096;
 }
 
+void free_payload_device(Payload &p) {
+  if (p.solver) dg_solver_destroy(p.solver);
+  if (p.mesh) dg_mesh_destroy(p.mesh);
+  p.solver = nullptr;
+  p.mesh = nullptr;
+}
+
+// the device side: one mesh and solver per running request, all advanced by
+// the persistent batch kernel on the server's stream
+struct DeviceEngine final : ServeEngine {
+  cudaStream_t stream = nullptr;
+  BatchCore *core = nullptr;
+  std::map<int64_t, Payload> pay;
+
+  int32_t finish_tick() override { return batch_core_check(core); }
+  int32_t start(int64_t id) override {
+    Payload &p = pay[id];
+    int32_t rc = dg_mesh_create(p.nv, p.xy.data(), p.nt, p.tri.data(), p.canon.empty() ? nullptr : p.canon.data(),
+                                p.bc.empty() ? nullptr : p.bc.data(), &p.mesh);
+    if (rc == DG_OK) rc = dg_init(p.mesh, &p.cfg, p.coeffs.data(), stream, &p.solver);
+    Scalars h{};
+    if (rc == DG_OK) rc = solver_read_scalars(p.solver, &h);
+    if (rc == DG_OK) {
+      h.t_end = p.t_end;
+      rc = solver_write_scalars(p.solver, &h);
+    }
+    if (rc != DG_OK) {
+      free_payload_device(p);
+      return rc;
+    }
+    p.xy.clear(); p.xy.shrink_to_fit();
+    p.tri.clear(); p.tri.shrink_to_fit();
+    return DG_OK;
+  }
+  int32_t poll(int64_t id, double *t, int64_t *steps, bool *bad) override {
+    Payload &p = pay[id];
+    Scalars h{};
+    const int32_t rc = solver_read_scalars(p.solver, &h);
+    if (rc != DG_OK) return rc;
+    *t = h.t;
+    *steps = h.steps;
+    *bad = h.nonphys > 0 || !std::isfinite(h.alpha);
+    return DG_OK;
+  }
+  int32_t retire(int64_t id, bool keep_result) override {
+    Payload &p = pay[id];
+    int32_t rc = DG_OK;
+    if (p.solver && keep_result) {
+      p.result.resize(p.coeffs.size());
+      double t = 0.0;
+      rc = dg_get_state(p.solver, p.result.data(), p.result.size(), &t);
+    }
+    free_payload_device(p);
+    p.xy.clear(); p.xy.shrink_to_fit();
+    p.tri.clear(); p.tri.shrink_to_fit();
+    p.coeffs.clear(); p.coeffs.shrink_to_fit();
+    return rc;
+  }
+  int32_t set_batch(const std::vector<int64_t> &running) override {
+    std::vector<dg_solver *> list;
+    for (int64_t id : running) list.push_back(pay[id].solver);
+    return batch_core_set_solves(core, list);
+  }
+  int32_t enqueue(int64_t nsteps) override { return batch_core_enqueue(core, nsteps); }
+};
+
 }  // namespace
 
 struct dg_server {
   int prec = 0;
-  size_t budget = 0, used = 0;
-  int steps_per_tick = 1;
-  cudaStream_t stream = nullptr;
   bool own_stream = false;
-  BatchCore *core = nullptr;
-  std::deque<int64_t> queue;
-  std::map<int64_t, Request> reqs;
-  std::vector<int64_t> running;
-  int64_t next_id = 1;
-  int64_t cell_stages = 0;
+  ServeScheduler sched;
+  DeviceEngine eng;
   std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+  dg_server(size_t budget, int steps_per_tick) : sched(budget, steps_per_tick) {}
   double now() const {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
   ~dg_server() {
-    if (stream) cudaStreamSynchronize(stream);
-    batch_core_delete(core);
-    for (auto &kv : reqs) {
-      if (kv.second.solver) dg_solver_destroy(kv.second.solver);
-      if (kv.second.mesh) dg_mesh_destroy(kv.second.mesh);
-    }
-    if (own_stream && stream) cudaStreamDestroy(stream);
+    if (eng.stream) cudaStreamSynchronize(eng.stream);
+    batch_core_delete(eng.core);
+    for (auto &kv : eng.pay) free_payload_device(kv.second);
+    if (own_stream && eng.stream) cudaStreamDestroy(eng.stream);
   }
 };
 
@@ -95,21 +152,19 @@ extern "C" int32_t dg_server_create(int32_t precision, size_t hbm_budget_bytes, 
   *out = nullptr;
   if ((precision != DG_PREC_FP64 && precision != DG_PREC_MIXED) || hbm_budget_bytes == 0 || steps_per_tick < 1)
     return set_error(DG_EINVAL, "bad precision, budget or steps per tick");
-  auto s = new (std::nothrow) dg_server();
+  auto s = new (std::nothrow) dg_server(hbm_budget_bytes, steps_per_tick);
   if (!s) return set_error(DG_ENOMEM, "host allocation failed");
   s->prec = precision;
-  s->budget = hbm_budget_bytes;
-  s->steps_per_tick = steps_per_tick;
   if (cuda_stream) {
-    s->stream = (cudaStream_t)cuda_stream;
+    s->eng.stream = (cudaStream_t)cuda_stream;
   } else {
-    if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    if (cudaStreamCreateWithFlags(&s->eng.stream, cudaStreamNonBlocking) != cudaSuccess) {
       delete s;
       return set_error(DG_ECUDA, "stream creation failed");
     }
     s->own_stream = true;
   }
-  int32_t rc = batch_core_new(precision, s->stream, &s->core);
+  int32_t rc = batch_core_new(precision, s->eng.stream, &s->eng.core);
   if (rc != DG_OK) { delete s; return rc; }
   *out = s;
   return DG_OK;
@@ -124,127 +179,35 @@ extern "C" int32_t dg_server_submit(dg_server *s, int64_t nv, const double *xy, 
     return set_error(DG_EINVAL, "bad request");
   if (cfg->precision != s->prec) return set_error(DG_EINVAL, "request precision differs from the server's");
   if (cfg->k != 1 && cfg->k != 2) return set_error(DG_EINVAL, "k must be 1 or 2");
-  Request r;
-  r.id = s->next_id++;
-  r.nv = nv;
-  r.nt = nt;
-  r.xy.assign(xy, xy + 2 * nv);
-  r.tri.assign(tri, tri + 3 * nt);
-  if (canon) r.canon.assign(canon, canon + nv);
-  if (bc) r.bc.assign(bc, bc + 3 * nt);
-  r.cfg = *cfg;
+  Payload p;
+  p.nv = nv;
+  p.nt = nt;
+  p.xy.assign(xy, xy + 2 * nv);
+  p.tri.assign(tri, tri + 3 * nt);
+  if (canon) p.canon.assign(canon, canon + nv);
+  if (bc) p.bc.assign(bc, bc + 3 * nt);
+  p.cfg = *cfg;
   const int nb = cfg->k == 1 ? 3 : 6;
-  r.coeffs.assign(coeffs, coeffs + 4 * nb * nt);
-  r.t_end = t_end;
-  r.bytes = solve_bytes(nt, cfg->k, s->prec);
-  r.submit_s = s->now();
-  *id = r.id;
-  s->queue.push_back(r.id);
-  s->reqs.emplace(r.id, std::move(r));
+  p.coeffs.assign(coeffs, coeffs + 4 * nb * nt);
+  p.t_end = t_end;
+  *id = s->sched.submit(nt, solve_bytes(nt, cfg->k, s->prec), t_end, s->now());
+  s->eng.pay.emplace(*id, std::move(p));
   return DG_OK;
-}
-
-static void retire(dg_server *s, Request &r, int32_t state, int32_t error) {
-  r.state = state;
-  r.error = error;
-  r.done_s = s->now();
-  if (r.solver) {
-    if (state == DG_REQ_DONE) {
-      r.result.resize(r.coeffs.size());
-      double t = 0.0;
-      if (dg_get_state(r.solver, r.result.data(), r.result.size(), &t) != DG_OK) {
-        r.state = DG_REQ_FAILED;
-        r.error = DG_ECUDA;
-      }
-      r.t = t;
-    }
-    dg_solver_destroy(r.solver);
-    r.solver = nullptr;
-  }
-  if (r.mesh) {
-    dg_mesh_destroy(r.mesh);
-    r.mesh = nullptr;
-  }
-  s->used -= std::min(s->used, r.bytes);
-  r.coeffs.clear();
-  r.coeffs.shrink_to_fit();
 }
 
 extern "C" int32_t dg_server_tick(dg_server *s, int32_t *n_running, int32_t *n_queued) {
   if (!s) return set_error(DG_EINVAL, "server is NULL");
-  // 1. finish the steps of the previous tick
-  int32_t rc = batch_core_check(s->core);
-  if (rc != DG_OK) return rc;
-  // 2. retire finished solves
-  bool changed = false;
-  std::vector<int64_t> still;
-  for (int64_t id : s->running) {
-    Request &r = s->reqs[id];
-    Scalars h{};
-    if ((rc = solver_read_scalars(r.solver, &h)) != DG_OK) return rc;
-    r.t = h.t;
-    r.steps = h.steps;
-    const bool bad = h.nonphys > 0 || !std::isfinite(h.alpha);
-    if (h.t >= r.t_end || bad) {
-      s->cell_stages += r.nt * 3 * h.steps;
-      retire(s, r, bad ? DG_REQ_FAILED : DG_REQ_DONE, bad ? DG_ENONPHYS : DG_OK);
-      changed = true;
-    } else {
-      still.push_back(id);
-    }
-  }
-  s->running.swap(still);
-  // 3. admit queued requests in order while their memory fits in the budget
-  while (!s->queue.empty()) {
-    Request &r = s->reqs[s->queue.front()];
-    if (r.bytes > s->budget) {   // can never fit
-      s->queue.pop_front();
-      retire(s, r, DG_REQ_FAILED, DG_ENOMEM);
-      continue;
-    }
-    if (s->used + r.bytes > s->budget) break;
-    s->queue.pop_front();
-    rc = dg_mesh_create(r.nv, r.xy.data(), r.nt, r.tri.data(), r.canon.empty() ? nullptr : r.canon.data(),
-                        r.bc.empty() ? nullptr : r.bc.data(), &r.mesh);
-    if (rc == DG_OK) rc = dg_init(r.mesh, &r.cfg, r.coeffs.data(), s->stream, &r.solver);
-    Scalars h{};
-    if (rc == DG_OK) rc = solver_read_scalars(r.solver, &h);
-    if (rc == DG_OK) {
-      h.t_end = r.t_end;
-      rc = solver_write_scalars(r.solver, &h);
-    }
-    if (rc != DG_OK) {
-      retire(s, r, DG_REQ_FAILED, rc);
-      continue;
-    }
-    r.xy.clear(); r.xy.shrink_to_fit();
-    r.tri.clear(); r.tri.shrink_to_fit();
-    r.state = DG_REQ_RUNNING;
-    r.start_s = s->now();
-    s->used += r.bytes;
-    s->running.push_back(r.id);
-    changed = true;
-  }
-  // 4. rebuild the batch when its membership changed, 5. enqueue the next steps
-  if (changed) {
-    std::vector<dg_solver *> list;
-    for (int64_t id : s->running) list.push_back(s->reqs[id].solver);
-    if ((rc = batch_core_set_solves(s->core, list)) != DG_OK) return rc;
-  }
-  if (!s->running.empty() && (rc = batch_core_enqueue(s->core, s->steps_per_tick)) != DG_OK) return rc;
-  if (n_running) *n_running = (int32_t)s->running.size();
-  if (n_queued) *n_queued = (int32_t)s->queue.size();
-  return DG_OK;
+  return s->sched.tick(s->eng, s->now(), n_running, n_queued);
 }
 
 extern "C" int32_t dg_server_request(const dg_server *s, int64_t id, dg_request_info *info) {
   if (!s || !info) return set_error(DG_EINVAL, "NULL argument");
-  auto it = s->reqs.find(id);
-  if (it == s->reqs.end()) return set_error(DG_EINVAL, "unknown request id");
-  const Request &r = it->second;
+  const SchedRequest *rp = s->sched.find(id);
+  if (!rp) return set_error(DG_EINVAL, "unknown request id");
+  const SchedRequest &r = *rp;
   info->state = r.state;
   info->error = r.error;
-  info->cells = r.nt;
+  info->cells = r.cells;
   info->steps = r.steps;
   info->t = r.t;
   info->t_end = r.t_end;
@@ -257,18 +220,18 @@ extern "C" int32_t dg_server_request(const dg_server *s, int64_t id, dg_request_
 
 extern "C" int32_t dg_server_result(dg_server *s, int64_t id, double *coeffs, size_t len) {
   if (!s || !coeffs) return set_error(DG_EINVAL, "NULL argument");
-  auto it = s->reqs.find(id);
-  if (it == s->reqs.end()) return set_error(DG_EINVAL, "unknown request id");
-  Request &r = it->second;
-  if (r.state != DG_REQ_DONE) return set_error(DG_EBUSY, "request not done");
-  if (len < r.result.size()) return set_error(DG_EINVAL, "output too small");
-  std::copy(r.result.begin(), r.result.end(), coeffs);
+  const SchedRequest *r = s->sched.find(id);
+  if (!r) return set_error(DG_EINVAL, "unknown request id");
+  if (r->state != DG_REQ_DONE) return set_error(DG_EBUSY, "request not done");
+  const std::vector<double> &res = s->eng.pay[id].result;
+  if (len < res.size()) return set_error(DG_EINVAL, "output too small");
+  std::copy(res.begin(), res.end(), coeffs);
   return DG_OK;
 }
 
 extern "C" int32_t dg_server_stats(const dg_server *s, int64_t *bytes_in_use, int64_t *cell_stages_done) {
   if (!s) return set_error(DG_EINVAL, "server is NULL");
-  if (bytes_in_use) *bytes_in_use = (int64_t)s->used;
-  if (cell_stages_done) *cell_stages_done = s->cell_stages;
+  if (bytes_in_use) *bytes_in_use = (int64_t)s->sched.used();
+  if (cell_stages_done) *cell_stages_done = s->sched.cell_stages();
   return DG_OK;
 }
