@@ -188,6 +188,23 @@ def oracle_rate(wl, steps, max_seconds=30.0):
     return wl.mesh.nt * 3 * done / el, done, el, O.num_threads()
 
 
+def cpu_baseline(wl, steps=10, max_seconds=25.0, single_core_seconds=8.0):
+    """The oracle timed on every host core (the reported baseline) and on one
+    core, on a bounded sample of the workload's steps."""
+    from oracle import oracle as O
+    rate, done, el, threads = oracle_rate(wl, steps=steps, max_seconds=max_seconds)
+    out = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"{done} oracle SSP-RK3 step(s) of the full {wl.mesh.nt}-cell workload ({el:.1f} s)"}
+    O.set_num_threads(1)
+    try:
+        r1, d1, e1, _ = oracle_rate(wl, steps=1, max_seconds=single_core_seconds)
+    finally:
+        O.set_num_threads(threads)
+    out["single_core"] = {"value": r1, "unit": UNIT, "cores": 1,
+                          "sample": f"{d1} oracle SSP-RK3 step(s) of the same workload ({e1:.1f} s)"}
+    return out
+
+
 def run_reference(args, world, rank):
     """Reference arm: the CPU oracle, each step one SSP-RK3 step of the DMR
     problem on a coarser grid of the same generator, sized so that the run
@@ -610,10 +627,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        wl_full = make_workload(args.workload, args.nx, args.ny)
-        rate, done, el, threads = oracle_rate(wl_full, steps=10, max_seconds=25.0)
-        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"{done} oracle SSP-RK3 step(s) of the full {nt}-cell workload ({el:.1f} s)"}
+        cpu = cpu_baseline(make_workload(args.workload, args.nx, args.ny))
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

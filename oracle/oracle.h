@@ -120,6 +120,8 @@ int or_step(const or_mesh *m, const or_config *cf, double *u, double *t, double 
 int or_advance(const or_mesh *m, const or_config *cf, double *u, double *t, double t_end,
                int64_t max_steps, int64_t *counters);
 int or_num_threads(void);
+/* threads of the OpenMP loops from now on (n > 0) */
+void or_set_num_threads(int n);
 
 /* ------------------------------------------------------------------------ */
 /* Scalar conservation laws u_t + div F(u) = 0, P1-P3 OEDG (Sec. 2; scalar.c)

@@ -87,6 +87,7 @@ def lib():
         L.or_step.argtypes = [P, P, P, P, dbl, P, P]
         L.or_advance.argtypes = [P, P, P, P, dbl, i64, P]
         L.or_num_threads.restype = C.c_int
+        L.or_set_num_threads.argtypes = [C.c_int]
         L.or_sc_basis.argtypes = [dbl, dbl, C.c_int, C.c_int, P]
         L.or_sc_mass_constants.argtypes = [C.c_int, P]
         L.or_sc_eval.argtypes = [P, C.c_int, P, i64, dbl, dbl]; L.or_sc_eval.restype = dbl
@@ -355,6 +356,10 @@ def mass_constants(k):
 
 def num_threads():
     return lib().or_num_threads()
+
+
+def set_num_threads(n):
+    lib().or_set_num_threads(int(n))
 
 
 def project_workload(om, wl):
