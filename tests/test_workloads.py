@@ -17,6 +17,7 @@
   from the stated ranges.
 """
 import math
+import re
 
 import numpy as np
 import pytest
@@ -170,3 +171,24 @@ def test_riemann4_quadrants():
             p = (W.GAMMA - 1.0) * (s[0, 3] - 0.5 * rho * v @ v)
             assert 0.1 <= rho <= 2.0 and 0.01 <= p <= 2.0 + 1e-12 and (np.abs(v) <= 1.0 + 1e-12).all()
     assert (wl.mesh.bc[wl.mesh.bc != 0] == W.BC_TRANSMISSIVE).all()
+
+
+def test_batch_and_serving_recipes():
+    """Batch: 64 solves, P1/P2 mixed, cells log-uniform in [2k, 200k] (about
+    2.8M expected; this seed gives 3.0M).  Serving: Poisson arrivals (times
+    increasing), sizes in [1k, 100k], three kinds of data, end times in range."""
+    ws = W.batch_workloads()
+    cells = np.array([w.mesh.nt for w in ws])
+    ks = {w.k for w in ws}
+    assert len(ws) == 64 and ks == {1, 2}
+    assert cells.min() >= 0.9 * 2000 and cells.max() <= 1.1 * 200000
+    assert 2.9e6 < cells.sum() < 3.1e6
+    assert all((w.mesh.bc[w.mesh.bc != 0] == W.BC_TRANSMISSIVE).all() for w in ws)
+    reqs = W.serving_requests(n=24)
+    at = np.array([a for _, _, a in reqs])
+    assert (np.diff(at) > 0).all() and at[0] > 0
+    assert all(0.005 <= te <= 0.02 for _, te, _ in reqs)
+    sizes = np.array([w.mesh.nt for w, _, _ in reqs])
+    assert sizes.min() >= 0.9 * 1000 and sizes.max() <= 1.1 * 100000
+    kinds = {re.match(r"[a-z]+", w.name).group(0) for w, _, _ in reqs}
+    assert kinds == {"vortex", "sedov", "riemann"}
