@@ -58,14 +58,24 @@ EXECUTED_FLOPS_P2 = {"rk": 1941.0, "stats": 739.0, "oe_bp": 1175.0}
 # DRAM bytes (read + write) per launch from the same captures (k_rk: mean of
 # its stages 1.596 / 1.807 / 1.807 GB).
 TRAFFIC_PER_LAUNCH = {"rk": 1.737e9, "stats": 0.947e9, "oe_bp": 1.376e9}
-# Mixed form (P2, FP32 modes and geometry, FP64 averages): algorithmic HBM
-# bytes per cell-stage, each array element moved once and neighbour data
-# taken from L2.  k_rk: u_n, v and u_h (3 x 112), geometry 80, own traces 144,
-# vertex records 192, Hessians 48.  k_stats: u_h 112, vertex records and
-# Hessians 240, per edge (1.5 per cell) 4 + 1 + 4 index bytes, normal 8 and
-# the 64-byte OE record.  k_oe_bp: u_h 112, geometry and indices 88, OE
-# records 1.5 x 64, internal nodes 16, output state 112, traces 144.
-ALGO_BYTES_MIXED_P2 = {"rk": 800.0, "stats": 474.0, "oe_bp": 552.0}
+# Mixed form (P2, FP32 modes 1-5 and FP64 averages: S = 4 x 8 + 4 x 5 x 4 =
+# 112 B of state per cell).  Algorithmic HBM bytes per cell-stage of the
+# method's three passes, each array element moved once and neighbour data
+# taken from L2: the flux pass reads u_n and v and writes u_h (the first
+# stage has v = u_n, read once: 2S; the others 3S) plus the geometry it needs
+# (FP32 inverse Jacobian 16, normals 24, lengths 12; FP64 |K| and 1/|K| 16;
+# neighbour indices 12: G1 = 80 B); the statistics pass reads u_h (S); the
+# OE + limiter pass reads u_h and writes u_sigma (2S) plus its geometry
+# (normals 24, OE lengths h and 1/h 24, limiter nodes 16, indices 12,
+# inverse Jacobian 16: G3 = 92 B).  A launch of the flux kernel
+# averages the three stages: (2 + 3 + 3) / 3 S + G1.
+S_MIXED_P2 = 112.0
+ALGO_BYTES_MIXED_P2 = {"rk": (8.0 / 3.0) * S_MIXED_P2 + 80.0, "stats": S_MIXED_P2,
+                       "oe_bp": 2.0 * S_MIXED_P2 + 92.0}
+# bytes the kernels' own design moves besides those: the exchange buffers
+# written by one pass and read by the next (traces of the stage input 144,
+# vertex records 192, Hessians 48, per-edge OE records 1.5 x 64 per cell)
+DESIGN_BYTES_MIXED_P2 = {"rk": 800.0, "stats": 474.0, "oe_bp": 552.0}
 # DRAM bytes per launch of the mixed-form kernels from one ncu capture
 TRAFFIC_MIXED_PER_LAUNCH = {"rk": 0.713e9, "stats": 0.495e9, "oe_bp": 0.554e9}
 
@@ -268,9 +278,15 @@ def main():
     ap.add_argument("--no-paper-meshes", action="store_true",
                     help="skip the forward-facing-step and wedge meshes")
     ap.add_argument("--no-scalar", action="store_true", help="skip the scalar conservation laws")
-    ap.add_argument("--to-t-end", type=float, default=0.0,
-                    help="also run the main workload to this end time in the mixed form and in FP64 "
-                         "(off by default: the FP64 run to t = 0.2 takes about 11 minutes)")
+    ap.add_argument("--to-t-end", type=float, default=0.2,
+                    help="run the DMR to this end time (0 = skip): both forms on a 480 x 120 grid, the mixed "
+                         "form on the main grid")
+    ap.add_argument("--to-t-end-grid", default="480x120",
+                    help="grid of the FP64 / mixed pair run to the end time")
+    ap.add_argument("--to-t-end-full-fp64", action="store_true",
+                    help="also run FP64 on the main grid to the end time (about 16 minutes at 1440 x 360)")
+    ap.add_argument("--sedov-t-end", type=float, default=0.0,
+                    help="run the Sedov blast (256 x 256, P2, FP64) to this end time (0 = skip)")
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-rate", type=float, default=30.0)
     args = ap.parse_args()
@@ -323,6 +339,11 @@ def main():
     value = nt * 3 * args.steps * world / (ms_max / 1e3)
 
     # roofline of the dominant kernel (instrumented pass of the same kernels on the same stream)
+    # measured DFMA throughput of this GPU: the roofline of the FP64 path
+    try:
+        fp64_meas, _ = N.probe_fma_peak(N.PREC_FP64)
+    except Exception:
+        fp64_meas = None
     roof = None
     if prof:
         kinds = {k: v for k, v in prof.items() if v[1] > 0}
@@ -332,10 +353,14 @@ def main():
         flops = ALGO_FLOPS_P2.get(dom, 0.0) * nt
         achieved = flops / (avg_ms / 1e3) / 1e12 if flops else None
         ex = EXECUTED_FLOPS_P2.get(dom)
-        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,
+        peak = fp64_meas if fp64_meas else FP64_PEAK_TFLOPS
+        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if achieved else None,
                 "traffic": TRAFFIC_PER_LAUNCH.get(dom),
-                "peak_source": "derived FP64 peak: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (of recipe nominal)",
+                "peak_source": ("measured DFMA throughput (dg_probe_fma_peak, this run)" if fp64_meas else
+                                "derived FP64 peak: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (of recipe nominal)"),
+                "peak_measured": fp64_meas, "peak_derived": FP64_PEAK_TFLOPS,
+                "frac_of_derived": achieved / FP64_PEAK_TFLOPS if achieved else None,
                 "algorithmic_flops_per_cell": ALGO_FLOPS_P2.get(dom),
                 "executed_flops_per_cell": ex,
                 "executed_tflops": ex * nt / (avg_ms / 1e3) / 1e12 if ex else None,
@@ -380,11 +405,16 @@ def main():
                 hbm = peaks.get("hbm_gbs", 6800.0)
                 if dom2 in ALGO_BYTES_MIXED_P2 and wl.k == 2:
                     gbs = ALGO_BYTES_MIXED_P2[dom2] * nt / (avg2 / 1e3) / 1e9
+                    dgbs = DESIGN_BYTES_MIXED_P2[dom2] * nt / (avg2 / 1e3) / 1e9
                     mixed["roofline"] = {"bound": "hbm", "kernel": dom2, "achieved": gbs, "peak": hbm, "unit": "GB/s",
                                          "frac": gbs / hbm, "traffic": TRAFFIC_MIXED_PER_LAUNCH.get(dom2),
                                          "peak_source": f"{peak_src} HBM copy bandwidth",
                                          "algorithmic_bytes_per_cell": ALGO_BYTES_MIXED_P2[dom2],
+                                         "design_bytes_per_cell": DESIGN_BYTES_MIXED_P2[dom2],
+                                         "design_frac": dgbs / hbm,
                                          "avg_launch_ms": avg2}
+                    mixed["step_hbm_frac"] = (sum(ALGO_BYTES_MIXED_P2.values()) * nt * 3 * args.steps
+                                              / (ms2 / 1e3) / 1e9 / hbm)
             del s2
             # density L1 difference from the FP64 path after the same number of steps
             n_l1 = 20
@@ -494,28 +524,73 @@ def main():
                                  "min_cfl_area_ratio": m_g.min_cfl_area(k, 0) / m_g.min_cfl_area(k, 1)}
         cfl_gain["paper_dmr_mean_dt_ratio"] = {"P1": 2.869570, "P2": 4.486689}
 
-    # the whole problem to an end time in both forms: steps, counters, wall
-    # time and the density L1 difference of the mixed form from FP64
+    # the problem to an end time: steps, counters (limited cells, cell averages
+    # outside G at any stage, CFL breaches), wall time, the smallest density,
+    # and the density L1 difference of the mixed form from FP64
     to_t_end = None
-    if args.to_t_end > 0.0:
-        to_t_end = {"t_end": args.to_t_end}
-        res = {}
-        for label, prec in (("mixed", N.PREC_MIXED), ("fp64", N.PREC_FP64)):
-            sv = N.Solver(mesh, N.config_for(wl, precision=prec), u0)
+    if args.to_t_end > 0.0 and args.workload == "dmr":
+        from paper_2409_09620_gb300 import workloads as W
+
+        def run_to_end(m, w, u, prec, T):
+            sv = N.Solver(m, N.config_for(w, precision=prec), u)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            st_e, _ = sv.advance(args.to_t_end)
+            st_e, rc_e = sv.advance(T, check=False)
             el = time.perf_counter() - t0
-            res[label] = sv.get_state()[0]
-            to_t_end[label] = {"steps": st_e["steps"], "t": st_e["t"], "seconds": el,
-                               "limited_cells": st_e["limited_cells"], "nonphysical": st_e["nonphysical"],
-                               "cfl_breaches": st_e["cfl_breaches"],
-                               "cell_stages_per_s": nt * 3 * st_e["steps"] / el}
+            ue = sv.get_state()[0]
             del sv
-        area = mesh.geometry(wl.k)["area"]
-        ra, rb = res["mixed"][0, 0], res["fp64"][0, 0]
-        to_t_end["density_l1_rel_mixed_vs_fp64"] = float((np.abs(ra - rb) * area).sum() / (np.abs(rb) * area).sum())
-        to_t_end["density_min"] = {"mixed": float(ra.min()), "fp64": float(rb.min())}
+            return ue, {"steps": st_e["steps"], "t": st_e["t"], "status": rc_e, "seconds": el,
+                        "limited_cells": st_e["limited_cells"], "nonphysical": st_e["nonphysical"],
+                        "cfl_breaches": st_e["cfl_breaches"], "alpha_last": st_e["alpha"],
+                        "density_min": float(ue[0, 0].min()),
+                        "cell_stages_per_s": m.nt * 3 * st_e["steps"] / el}
+
+        def density_l1(m, w, a, b):
+            area = m.geometry(w.k)["area"]
+            return float((np.abs(a[0, 0] - b[0, 0]) * area).sum() / (np.abs(b[0, 0]) * area).sum())
+
+        T = args.to_t_end
+        to_t_end = {"t_end": T}
+        gx, gy = (int(v) for v in args.to_t_end_grid.split("x"))
+        w_r = W.dmr_workload(nx=gx, ny=gy, k=2)
+        m_r = N.Mesh.from_mesh(w_r.mesh)
+        u_r = N.initial_state(m_r, w_r)
+        ua, ra = run_to_end(m_r, w_r, u_r, N.PREC_MIXED, T)
+        ub, rb = run_to_end(m_r, w_r, u_r, N.PREC_FP64, T)
+        to_t_end[f"dmr{gx}x{gy}"] = {"cells": w_r.mesh.nt, "mixed": ra, "fp64": rb,
+                                     "density_l1_rel_mixed_vs_fp64": density_l1(m_r, w_r, ua, ub),
+                                     "speedup_mixed_vs_fp64": rb["seconds"] / ra["seconds"]}
+        del m_r
+        uf, rf = run_to_end(mesh, wl, u0, N.PREC_MIXED, T)
+        full = {"cells": nt, "mixed": rf}
+        if args.to_t_end_full_fp64:
+            ug, rg = run_to_end(mesh, wl, u0, N.PREC_FP64, T)
+            full["fp64"] = rg
+            full["density_l1_rel_mixed_vs_fp64"] = density_l1(mesh, wl, uf, ug)
+            full["speedup_mixed_vs_fp64"] = rg["seconds"] / rf["seconds"]
+        to_t_end[f"{args.workload}{args.nx}x{args.ny}"] = full
+        del uf
+
+    sedov = None
+    if args.sedov_t_end > 0.0:
+        from paper_2409_09620_gb300 import workloads as W
+        w_s = W.sedov_workload(n=256, k=2)
+        m_s = N.Mesh.from_mesh(w_s.mesh)
+        sv = N.Solver(m_s, N.config_for(w_s), N.initial_state(m_s, w_s))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st_s, rc_s = sv.advance(args.sedov_t_end, check=False)
+        el = time.perf_counter() - t0
+        us_, _ = sv.get_state()
+        area = m_s.geometry(2)["area"]
+        sedov = {"workload": "sedov256x256_P2 (131,072 cells), FP64", "t_end": args.sedov_t_end,
+                 "steps": st_s["steps"], "t": st_s["t"], "status": rc_s, "seconds": el,
+                 "limited_cells": st_s["limited_cells"], "nonphysical": st_s["nonphysical"],
+                 "cfl_breaches": st_s["cfl_breaches"], "density_min": float(us_[0, 0].min()),
+                 "density_max": float(us_[0, 0].max()),
+                 "mass": float((us_[0, 0] * area).sum()), "energy": float((us_[3, 0] * area).sum()),
+                 "cell_stages_per_s": m_s.nt * 3 * st_s["steps"] / el}
+        del sv, m_s
 
     # the paper's own domains (Sec. 5) on near-equilateral lattice meshes of
     # about its cell counts: throughput, and the mean BP time step of the
@@ -588,15 +663,15 @@ def main():
             for k in (1, 2, 3):
                 rows, prev = [], None
                 for lev in levels:
-                    wl = make(level=lev, k=k)
-                    m = N.Mesh.from_mesh(wl.mesh)
-                    u = N.scalar_project(m, k, wl.u0)
-                    cf = N.make_scalar_config(k, flux=wl.flux, cfl=0.5 ** ((lev - 1) / 3.0) if k == 3 else 1.0)
+                    wl_s = make(level=lev, k=k)
+                    m = N.Mesh.from_mesh(wl_s.mesh)
+                    u = N.scalar_project(m, k, wl_s.u0)
+                    cf = N.make_scalar_config(k, flux=wl_s.flux, cfl=0.5 ** ((lev - 1) / 3.0) if k == 3 else 1.0)
                     sv = N.ScalarSolver(m, cf, u)
-                    st_s = sv.advance(wl.t_end)
+                    st_s = sv.advance(wl_s.t_end)
                     xy = m.quad_points()
-                    e = np.array(sv.errors(wl.exact(xy[..., 0], xy[..., 1], wl.t_end)))
-                    row = {"cells": wl.mesh.nt, "steps": st_s["steps"], "L1": e[0], "L2": e[1], "Linf": e[2]}
+                    e = np.array(sv.errors(wl_s.exact(xy[..., 0], xy[..., 1], wl_s.t_end)))
+                    row = {"cells": wl_s.mesh.nt, "steps": st_s["steps"], "L1": e[0], "L2": e[1], "Linf": e[2]}
                     if prev is not None:
                         row["order"] = [float(v) for v in np.log2(prev / e)]
                     rows.append(row)
@@ -641,9 +716,10 @@ def main():
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": 19 * args.steps, "clocks": clocks, "fp32": mixed, "batch": batch,
                 "serving": serving, "bp_cfl_gain": cfl_gain, "paper_meshes": paper_meshes, "scalar": scalar,
-                "to_t_end": to_t_end,
+                "to_t_end": to_t_end, "sedov_to_t_end": sedov,
                 "peaks": {"source": peak_src, "hbm_gbs": peaks.get("hbm_gbs")},
-                "stats": {"limited_cells": st["limited_cells"], "cfl_breaches": st["cfl_breaches"],
+                "stats": {"limited_cells": st["limited_cells"], "nonphysical": st["nonphysical"],
+                          "cfl_breaches": st["cfl_breaches"],
                           "t": st["t"], "dt_last": st["dt_last"]}}
         print(json.dumps(line), flush=True)
     barrier(world)

@@ -170,6 +170,16 @@ int32_t dg_set_state(dg_solver *solver, const double *coeffs, double t);
  * fin_alpha (alpha, counters, time).  A step is 19 launches (13 with OE off). */
 #define DG_NUM_KERNEL_KINDS 7
 int32_t dg_profile_steps(dg_solver *solver, int64_t n, double *ms, int64_t *launches);
+/* Measured FMA throughput of the current device: a kernel of independent
+ * fused multiply-add chains (2 flops each) on every SM, timed with CUDA
+ * events on cuda_stream (a cudaStream_t, NULL = the legacy default stream);
+ * the best of three launches after a warm-up, about 20 ms each.  precision
+ * DG_PREC_FP64 measures DFMA, DG_PREC_MIXED measures FFMA.  *tflops receives
+ * TFLOP/s and *ms (nullable) the launch time.  Not part of the paper: the
+ * FP64 stage kernels are bound by the FP64 pipe on GB300, and this is the
+ * peak their roofline fraction is taken against.  Errors: DG_EINVAL,
+ * DG_ECUDA. */
+int32_t dg_probe_fma_peak(int32_t precision, double *tflops, double *ms, void *cuda_stream);
 /* the solver's CUDA stream (cudaStream_t) */
 void *dg_stream(const dg_solver *solver);
 void dg_solver_destroy(dg_solver *solver);
@@ -217,9 +227,20 @@ int32_t dg_batch_create(int32_t n, const dg_mesh *const *meshes, const dg_config
 void dg_batch_destroy(dg_batch *batch);
 /* Advance every solve i until t_i >= t_end[i] (t_end NULL: +inf) or max_steps
  * steps; solves that reached their end time idle.  stats (nullable) receives n
- * entries.  In form 1, a grid barrier that waits longer than 2 s ends the
- * launch early and the call returns DG_ETIMEOUT. */
+ * entries.  In form 1, a grid barrier that waits longer than its limit (2 s
+ * unless set by dg_batch_set_barrier) ends the launch early and the call
+ * returns DG_ETIMEOUT. */
 int32_t dg_batch_advance(dg_batch *batch, const double *t_end, int64_t max_steps, dg_stats *stats);
+/* Wait limit of the grid barriers of the cooperative form (default 2 s per
+ * wait; a block whose wait runs out ends the launch, and the next
+ * dg_batch_advance / dg_batch_sync returns DG_ETIMEOUT after clearing the
+ * barrier and the solves' finalisation tickets; the solves' states are then
+ * those of an interrupted step, to be restored with dg_set_state).
+ * extra_arrivals is a fault-injection hook for tests: it raises the number of
+ * arrivals the barrier waits for above the grid size, so that every wait runs
+ * out; 0 in normal use.  DG_EINVAL for timeout_ns <= 0 or extra_arrivals < 0.
+ * The paper has no counterpart (the batch is an interface addition). */
+int32_t dg_batch_set_barrier(dg_batch *batch, int64_t timeout_ns, int32_t extra_arrivals);
 /* enqueue exactly n steps of every solve; pair with dg_batch_sync */
 int32_t dg_batch_advance_async(dg_batch *batch, int64_t nsteps);
 int32_t dg_batch_sync(dg_batch *batch);
@@ -313,7 +334,6 @@ int32_t dg_server_stats(const dg_server *server, int64_t *bytes_in_use, int64_t 
 int32_t dg_stats_noalloc(const dg_mesh *mesh, int32_t k, const double *coeffs, double *stats,
                          void *cuda_stream);
 
-/* thread-local message of the last error */
 /* ---------------------------------------------------------------------- */
 /* Scalar conservation laws u_t + div F(u) = 0: the OEDG scheme of Sec. 2   */
 /* (DG operator eq. DGScalar:Dis with the LF flux eq. fluxLF; OE procedure  */
@@ -361,6 +381,7 @@ int32_t dg_scalar_get_state(const dg_scalar *solver, double *coeffs, size_t len,
 int32_t dg_scalar_errors(const dg_scalar *solver, const double *exact, double *out3);
 void dg_scalar_destroy(dg_scalar *solver);
 
+/* thread-local message of the last failure in the calling thread */
 const char *dg_last_error(void);
 
 #ifdef __cplusplus

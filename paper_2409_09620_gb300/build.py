@@ -17,6 +17,7 @@ ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libdg_gb300.so")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["dg_kernels.cu", "dg_api.cu", "dg_noalloc.cu", "dg_batch.cu", "dg_serve.cu", "dg_scalar.cu",
+           "dg_probe.cu",
            "dg_mesh_host.cpp", "dg_serve_sched.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",

@@ -43,12 +43,18 @@ struct WorkItem {
   int64_t first_tile, ntiles;
 };
 
+// Grid barrier of the cooperative form.  count and gen are the barrier;
+// error is set by a block whose wait ran out; extra phantom arrivals (0 in
+// normal use) raise the count the barrier waits for, so that a test can make
+// every wait run out; timeout_ns bounds each wait.
 struct BarrierState {
   unsigned int count;
   unsigned int gen;
   int error;
-  int pad;
+  unsigned int extra;
+  unsigned long long timeout_ns;
 };
+constexpr unsigned long long BARRIER_TIMEOUT_NS = 2000000000ull;
 
 __constant__ double kRK_A[3] = {0.0, 0.75, 1.0 / 3.0};
 __constant__ double kRK_B[3] = {1.0, 0.25, 2.0 / 3.0};
@@ -62,24 +68,32 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 // Grid-wide barrier for a cooperative launch (all blocks resident).  The wait
-// is bounded: after 2 s the block records an error and leaves; every block
-// then returns false and the kernel ends early (the host reports DG_ETIMEOUT).
+// is bounded: after timeout_ns (or, should the global timer not advance, a
+// number of polls far beyond it) the block records an error and leaves; a
+// waiting block also leaves as soon as another block has recorded one.
+// Every block then returns false and the kernel ends early (the host reports
+// DG_ETIMEOUT).
 __device__ __forceinline__ bool grid_sync(BarrierState *b, unsigned nblocks) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned *vgen = &b->gen;
+    volatile int *verr = &b->error;
+    const unsigned target = nblocks + *(volatile unsigned *)&b->extra;
+    const unsigned long long limit = *(volatile unsigned long long *)&b->timeout_ns;
     const unsigned g = *vgen;
     __threadfence();
     const unsigned arrived = atomicAdd(&b->count, 1u);
-    if (arrived == nblocks - 1) {
+    if (arrived == target - 1) {
       atomicExch(&b->count, 0u);
       __threadfence();
       atomicAdd(&b->gen, 1u);
     } else {
       const unsigned long long t0 = global_ns();
-      while (*vgen == g) {
-        if (global_ns() - t0 > 2000000000ull) {
+      const unsigned long long max_polls = limit / 16 + 1000000ull;   // a poll takes far longer than 16 ns
+      unsigned long long polls = 0;
+      while (*vgen == g && *verr == 0) {
+        if (global_ns() - t0 > limit || ++polls > max_polls) {
           atomicExch(&b->error, 1);
           break;
         }
@@ -87,7 +101,7 @@ __device__ __forceinline__ bool grid_sync(BarrierState *b, unsigned nblocks) {
       }
     }
     __threadfence();
-    s_ok = *(volatile int *)&b->error == 0;
+    s_ok = *verr == 0;
   }
   __syncthreads();
   return s_ok;
@@ -231,6 +245,8 @@ struct BatchCore {
   WorkItem *d_work = nullptr;
   size_t work_cap = 0;
   BarrierState *d_bar = nullptr;
+  unsigned long long bar_timeout_ns = BARRIER_TIMEOUT_NS;
+  unsigned bar_extra = 0;
   int nwork = 0, grid = 0, cpb = 4 * TPB, blocks_per_sm = 0, num_sms = 0, form = 3;
   int occ_fused = 0, occ_phase[3] = {0, 0, 0}, grid_phase[3] = {0, 0, 0};
   cudaGraphExec_t exec = nullptr;
@@ -261,7 +277,14 @@ struct BatchCore {
     form = 3;
     blocks_per_sm = max_blocks_per_sm(form);
     if (cudaMalloc(&d_bar, sizeof(BarrierState)) != cudaSuccess) return set_error(DG_ENOMEM, "barrier state");
+    return reset_barrier();
+  }
+
+  // a fresh barrier (no arrivals, no error) with the configured wait limit
+  int32_t reset_barrier() {
     BarrierState z{};
+    z.extra = bar_extra;
+    z.timeout_ns = bar_timeout_ns;
     if (cudaMemcpy(d_bar, &z, sizeof(z), cudaMemcpyHostToDevice) != cudaSuccess) return set_error(DG_ECUDA, "barrier");
     return DG_OK;
   }
@@ -420,8 +443,7 @@ struct BatchCore {
         cudaStreamSynchronize(stream) != cudaSuccess)
       return set_error(DG_ECUDA, "batch sync");
     if (h.error) {
-      BarrierState z{};
-      cudaMemcpy(d_bar, &z, sizeof(z), cudaMemcpyHostToDevice);
+      reset_barrier();
       // blocks that left early may hold finalisation tickets: clear them
       for (const SolveDev &d : host_sv)
         cudaMemset(d.fin.tick, 0, 3 * ticket_slots(d.ntiles) * sizeof(unsigned));
@@ -496,6 +518,14 @@ extern "C" int32_t dg_batch_shape(const dg_batch *b, int32_t *cells_per_block, i
   if (grid) *grid = b->core.grid;
   if (graph) *graph = b->core.graph_ok ? 1 : 0;
   return DG_OK;
+}
+
+extern "C" int32_t dg_batch_set_barrier(dg_batch *b, int64_t timeout_ns, int32_t extra_arrivals) {
+  if (!b || timeout_ns <= 0 || extra_arrivals < 0) return set_error(DG_EINVAL, "bad argument");
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return set_error(DG_ECUDA, "sync");
+  b->core.bar_timeout_ns = (unsigned long long)timeout_ns;
+  b->core.bar_extra = (unsigned)extra_arrivals;
+  return b->core.reset_barrier();
 }
 
 extern "C" int32_t dg_batch_advance_async(dg_batch *b, int64_t nsteps) {

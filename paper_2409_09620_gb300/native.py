@@ -83,11 +83,13 @@ SIGNATURES = {
     "dg_op_limit": (i32, [P, P, P, P]),
     "dg_op_alpha": (i32, [P, P, dbl, C.POINTER(dbl)]),
     "dg_profile_steps": (i32, [P, i64, P, P]),
+    "dg_probe_fma_peak": (i32, [i32, C.POINTER(dbl), C.POINTER(dbl), P]),
     "dg_stats_noalloc": (i32, [P, i32, P, P, P]),
     "dg_batch_create": (i32, [i32, P, P, P, P, C.POINTER(P)]),
     "dg_batch_destroy": (None, [P]),
     "dg_batch_advance": (i32, [P, P, i64, P]),
     "dg_batch_advance_async": (i32, [P, i64]),
+    "dg_batch_set_barrier": (i32, [P, i64, i32]),
     "dg_batch_sync": (i32, [P]),
     "dg_batch_solver": (i32, [P, i32, C.POINTER(P)]),
     "dg_batch_set_shape": (i32, [P, i32, i32, i32]),
@@ -147,6 +149,13 @@ def make_config(k, precision=PREC_FP64, oe=OE_RI, bp=BP_ON, decomp=DECOMP_OPTIMA
     cf.shock_x0, cf.shock_angle, cf.shock_speed = float(shock[0]), float(shock[1]), float(shock[2])
     cf.shock_pre, cf.shock_post = int(shock[3]), int(shock[4])
     return cf
+
+
+def probe_fma_peak(precision=PREC_FP64, stream=None):
+    """Measured FMA throughput of the current device (TFLOP/s, launch ms)."""
+    tf, ms = dbl(), dbl()
+    _check(lib().dg_probe_fma_peak(precision, C.byref(tf), C.byref(ms), None if stream is None else P(stream)))
+    return tf.value, ms.value
 
 
 def config_for(workload, **kw):
@@ -375,6 +384,11 @@ class Batch:
 
     def sync(self):
         _check(lib().dg_batch_sync(self.h))
+
+    def set_barrier(self, timeout_ns=2_000_000_000, extra_arrivals=0):
+        """Wait limit of the cooperative form's grid barriers; extra_arrivals > 0
+        (tests only) makes every barrier wait run out."""
+        _check(lib().dg_batch_set_barrier(self.h, int(timeout_ns), int(extra_arrivals)))
 
     def set_shape(self, cells_per_block, blocks_per_sm, launches_per_stage=3):
         _check(lib().dg_batch_set_shape(self.h, cells_per_block, blocks_per_sm, launches_per_stage))

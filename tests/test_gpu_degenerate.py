@@ -124,7 +124,9 @@ def test_periodic_two_by_two_rejected(oracle_mod, N):
 @pytest.mark.parametrize("precision", [0, 1])
 def test_degenerate_meshes_in_a_batch(oracle_mod, N, precision, form):
     """A batch of the tiny meshes (1, 2, 8 and 132 cells, P1 and P2) is
-    bitwise the solves run alone, in both launch forms."""
+    bitwise the solves run alone, in both launch forms, and matches the
+    oracle."""
+    from tests.test_gpu_batch import check_against_oracle
     wls = [_case("one_cell", 1), _case("two_cells", 2), _case("dmr_8", 2), _case("two_tiles_ragged", 1)]
     O = oracle_mod
     meshes = [N.Mesh.from_mesh(w.mesh) for w in wls]
@@ -140,3 +142,4 @@ def test_degenerate_meshes_in_a_batch(oracle_mod, N, precision, form):
         a, ta = batch.solver(i).get_state()
         b, tb = solo.get_state()
         assert ta == tb and np.array_equal(a, b), i
+        check_against_oracle(O, wls[i], us[i], a, ta, 6, precision)

@@ -1,10 +1,12 @@
 """GPU tests of the continuous-batching server: results are the same alone and
-in a mix of concurrently running requests, admission respects the HBM budget,
-and a request larger than the budget fails cleanly."""
+in a mix of concurrently running requests, and match the CPU oracle run to
+the same end time; admission respects the HBM budget, and a request larger
+than the budget fails cleanly."""
 import numpy as np
 import pytest
 
 from paper_2409_09620_gb300 import workloads as W
+from tests.test_gpu_batch import check_against_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -16,9 +18,13 @@ def N():
     return native
 
 
-def _request(N, wl, precision=0):
-    m = N.Mesh.from_mesh(wl.mesh)
-    u = N.initial_state(m, wl)
+def _request(N, wl, precision=0, O=None):
+    """(workload, configuration, initial state): the oracle's projection and
+    limiter pass when O is given, else the library's projection."""
+    if O is not None:
+        u = O.project_workload(O.OracleMesh.from_mesh(wl.mesh), wl)
+    else:
+        u = N.initial_state(N.Mesh.from_mesh(wl.mesh), wl)
     return wl, N.config_for(wl, precision=precision), u
 
 
@@ -31,8 +37,8 @@ def _drain(srv, max_ticks=100000):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-def test_same_alone_and_in_the_mix(N, precision):
-    target = _request(N, W.riemann4_workload(n=17, k=2, seed=21), precision)
+def test_same_alone_and_in_the_mix(oracle_mod, N, precision):
+    target = _request(N, W.riemann4_workload(n=17, k=2, seed=21), precision, oracle_mod)
     others = [_request(N, w, precision) for w in
               (W.vortex_workload(n=20, k=1), W.sedov_workload(n=16, k=2), W.riemann4_workload(n=9, k=1, seed=5),
                W.dmr_workload(nx=30, ny=10, k=2))]
@@ -63,6 +69,8 @@ def test_same_alone_and_in_the_mix(N, precision):
     assert np.array_equal(srv.result(rid), alone)
     for i in ids:
         assert srv.info(i)["state"] == N.REQ_DONE
+    # the oracle run to the same end time from the same state
+    check_against_oracle(oracle_mod, target[0], target[2], alone, t_end, steps_alone, precision, t_end=t_end)
     # and the same as the solver used on its own
     solo = N.Solver(N.Mesh.from_mesh(target[0].mesh), target[1], target[2])
     solo.advance(t_end)
