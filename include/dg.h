@@ -173,7 +173,9 @@ int32_t dg_profile_steps(dg_solver *solver, int64_t n, double *ms, int64_t *laun
 /* Measured FMA throughput of the current device: a kernel of independent
  * fused multiply-add chains (2 flops each) on every SM, timed with CUDA
  * events on cuda_stream (a cudaStream_t, NULL = the legacy default stream);
- * the best of three launches after a warm-up, about 20 ms each.  precision
+ * two launch shapes (8 or 16 chains per thread, 2048 or 1024 threads per
+ * SM), each the best of three launches after a warm-up, about 10-20 ms each;
+ * the faster shape's rate is reported.  precision
  * DG_PREC_FP64 measures DFMA, DG_PREC_MIXED measures FFMA.  *tflops receives
  * TFLOP/s and *ms (nullable) the launch time.  Not part of the paper: the
  * FP64 stage kernels are bound by the FP64 pipe on GB300, and this is the
@@ -321,7 +323,8 @@ int32_t dg_server_stats(const dg_server *server, int64_t *bytes_in_use, int64_t 
  * this is an interface addition.
  *
  * coeffs is a DEVICE modal state [4][nb][nt] (layout above, nb from k) and
- * stats a DEVICE array of 10 doubles, both owned by the caller; the work is
+ * stats a DEVICE array of 10 doubles, both owned by the caller and on the
+ * device that holds the mesh, which must be the current device; the work is
  * enqueued on cuda_stream (a cudaStream_t, NULL = the legacy default stream)
  * and the call returns without synchronising.  The call allocates nothing: its
  * scratch is a fixed 2.36 MB device array inside the library, which every GPU
@@ -330,7 +333,8 @@ int32_t dg_server_stats(const dg_server *server, int64_t *bytes_in_use, int64_t 
  * so make the first call on each device before any stream capture.  All calls
  * on a device share the array and it keeps the last call's contents: calls
  * whose kernels overlap on the same GPU race.  Errors: DG_EINVAL (NULL
- * argument, k not 1 or 2, more than 4,194,304 cells), DG_ECUDA. */
+ * argument, k not 1 or 2, more than 4,194,304 cells, the current device is
+ * not the mesh's), DG_ECUDA. */
 int32_t dg_stats_noalloc(const dg_mesh *mesh, int32_t k, const double *coeffs, double *stats,
                          void *cuda_stream);
 

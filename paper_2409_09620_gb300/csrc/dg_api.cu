@@ -66,6 +66,7 @@ struct dg_mesh {
   double *psi_node = nullptr;
   double min_ca[4] = {0, 0, 0, 0};   // (P1 optimal, P1 ZXS, P2 optimal, P2 ZXS)
   double area_total = 0.0;
+  int device = 0;                    // the CUDA device that holds the mesh's arrays
   ~dg_mesh() {
     cudaFree(area); cudaFree(jinv); cudaFree(nrm); cudaFree(len); cudaFree(vxy); cudaFree(node);
     cudaFree(c_area); cudaFree(limv); cudaFree(conn); cudaFree(hgeo);
@@ -109,6 +110,7 @@ void mesh_view(const dg_mesh *mesh, int64_t *nt, const double **area, double *ar
   *area_total = mesh->area_total;
 }
 int32_t set_error(int32_t code, const char *msg) { return fail(code, "%s", msg); }
+int mesh_device(const dg_mesh *mesh) { return mesh->device; }
 }  // namespace dg
 
 // ============================================================================
@@ -126,6 +128,7 @@ extern "C" int32_t dg_mesh_create(int64_t nv, const double *xy, int64_t nt, cons
   if (!m) return fail(DG_ENOMEM, "host allocation failed");
   m->nv = nv;
   m->nt = nt;
+  if (cudaGetDevice(&m->device) != cudaSuccess) { delete m; return fail(DG_ECUDA, "no CUDA device"); }
   m->nbr = std::move(hm.nbr);
   m->nbr_edge = std::move(hm.nbr_edge);
   m->bnd_tag = std::move(hm.bnd_tag);
@@ -414,10 +417,11 @@ extern "C" int32_t dg_init(const dg_mesh *mesh, const dg_config *cfg, const doub
   STRY(alloc_state(s, &s->un));
   STRY(alloc_state(s, &s->uh));
   STRY(alloc_state(s, &s->us));
-  STRY(cudaMalloc(&s->tr, rs * nt * 3 * nq * trace_stride(cfg->precision)));
-  STRY(cudaMalloc(&s->vd, rs * nt * VD_CELL));
-  STRY(cudaMalloc(&s->hs, rs * nt * 12));
-  STRY(cudaMalloc(&s->ej, rs * std::max<int64_t>(mesh->ne, 1) * EJ_STRIDE));
+  const int64_t xc = uses_exchange(cfg->precision) ? nt : 1;   // exchange buffers: FP64 form only
+  STRY(cudaMalloc(&s->tr, rs * xc * 3 * nq * trace_stride(cfg->precision)));
+  STRY(cudaMalloc(&s->vd, rs * xc * VD_CELL));
+  STRY(cudaMalloc(&s->hs, rs * xc * 12));
+  STRY(cudaMalloc(&s->ej, rs * (uses_exchange(cfg->precision) ? std::max<int64_t>(mesh->ne, 1) : 1) * EJ_STRIDE));
   STRY(dalloc(&s->part_sum, 4 * nblk));
   STRY(dalloc(&s->part_dev, 5 * nblk));
   STRY(dalloc(&s->part_alpha, nblk));
@@ -623,7 +627,7 @@ extern "C" int32_t dg_profile_steps(dg_solver *s, int64_t n, double *ms, int64_t
         rec(3, [&] { launch_stats_only(c, s->uh, C_OUT[st]); });
         rec(4, [&] { launch_fin_dev(c); });
       }
-      rec(5, [&] { launch_oe_bp_only(c, s->uh, st == 2 ? s->un : s->us, oe, bp, C_OUT[st]); });
+      rec(5, [&] { launch_oe_bp_only(c, s->uh, st == 2 ? s->un : s->us, oe, bp, C_OUT[st], st == 2); });
       rec(6, [&] { launch_fin_alpha(c, st); });
     }
     cudaError_t e = cudaStreamSynchronize(s->stream);

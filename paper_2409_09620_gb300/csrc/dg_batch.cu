@@ -170,10 +170,10 @@ __device__ __forceinline__ void phase_oe_bp(const SolveDev *__restrict__ sv, con
     for (int64_t t = it.first_tile; t < it.first_tile + it.ntiles; ++t) {
       if (S.k == 1)
         oe_bp_tile<1, Real>(S.mesh, S.ph, uh, out, (const Real *)S.ej, (Real *)S.tr, S.part_alpha, S.part_cnt,
-                            S.sc, S.oe != 0, S.bp != 0, c_out, t);
+                            S.sc, S.oe != 0, S.bp != 0, c_out, stage == 2, t);
       else
         oe_bp_tile<2, Real>(S.mesh, S.ph, uh, out, (const Real *)S.ej, (Real *)S.tr, S.part_alpha, S.part_cnt,
-                            S.sc, S.oe != 0, S.bp != 0, c_out, t);
+                            S.sc, S.oe != 0, S.bp != 0, c_out, stage == 2, t);
       finish_alpha(S.part_alpha, S.part_cnt, S.fin, t, S.ntiles, S.sc, stage);
     }
   }
@@ -618,15 +618,16 @@ extern "C" int32_t dg_batch_autotune(dg_batch *b, int32_t steps, int32_t *best_c
     StateBuf un, uh, us;
     solver_states(s, &un, &uh, &us);
     Snap &q = snaps[i];
-    q = Snap{nullptr, nullptr, nullptr, sizeof(double) * 4 * nt, rs * 4 * (nb - 1) * nt, rs * nt * 3 * nq * trace_stride(core.prec), {}};
+    const size_t ntr = uses_exchange(core.prec) ? rs * nt * 3 * nq * trace_stride(core.prec) : 0;
+    q = Snap{nullptr, nullptr, nullptr, sizeof(double) * 4 * nt, rs * 4 * (nb - 1) * nt, ntr, {}};
     if (cudaMalloc(&q.avg, q.navg) != cudaSuccess || cudaMalloc(&q.hi, q.nhi) != cudaSuccess ||
-        cudaMalloc(&q.tr, q.ntr) != cudaSuccess) {
+        (q.ntr && cudaMalloc(&q.tr, q.ntr) != cudaSuccess)) {
       free_snaps();
       return set_error(DG_ENOMEM, "autotune snapshot");
     }
     cudaMemcpyAsync(q.avg, un.avg, q.navg, cudaMemcpyDeviceToDevice, core.stream);
     cudaMemcpyAsync(q.hi, un.hi, q.nhi, cudaMemcpyDeviceToDevice, core.stream);
-    cudaMemcpyAsync(q.tr, solver_ctx(s).tr, q.ntr, cudaMemcpyDeviceToDevice, core.stream);
+    if (q.ntr) cudaMemcpyAsync(q.tr, solver_ctx(s).tr, q.ntr, cudaMemcpyDeviceToDevice, core.stream);
     if (solver_read_scalars(s, &q.sc) != DG_OK) { free_snaps(); return DG_ECUDA; }
   }
   cudaEvent_t e0, e1;
@@ -659,7 +660,7 @@ extern "C" int32_t dg_batch_autotune(dg_batch *b, int32_t steps, int32_t *best_c
     const Snap &q = snaps[i];
     cudaMemcpyAsync(un.avg, q.avg, q.navg, cudaMemcpyDeviceToDevice, core.stream);
     cudaMemcpyAsync(un.hi, q.hi, q.nhi, cudaMemcpyDeviceToDevice, core.stream);
-    cudaMemcpyAsync(solver_ctx(s).tr, q.tr, q.ntr, cudaMemcpyDeviceToDevice, core.stream);
+    if (q.ntr) cudaMemcpyAsync(solver_ctx(s).tr, q.tr, q.ntr, cudaMemcpyDeviceToDevice, core.stream);
     if (solver_write_scalars(s, &q.sc) != DG_OK) { free_snaps(); return DG_ECUDA; }
   }
   free_snaps();

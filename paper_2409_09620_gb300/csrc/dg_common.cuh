@@ -7,7 +7,9 @@
 //             len[3][nt], hgeo[6][nt] (h_i, 1/h_i), vxy[6][nt], node[4][nt] (P2 internal
 //             nodes, reference coords),
 //             limv[2][nt] (P1 limiter vertices), conn[3][nt] (neighbour << 2 | its edge, or -tag)
-//   exchange  tr[nt][3][Q][8]  traces of the stage input at edge Gauss points:
+//   exchange buffers (FP64 form only; the mixed form's passes read the
+//   neighbours' modal states instead, see dg_stage_mixed.cuh):
+//             tr[nt][3][Q][8]  traces of the stage input at edge Gauss points:
 //                              u (4) and F(u).n_i (4), written by the cell that owns them
 //             vd[nt][3][16]    value (4), physical gradient (8), 1/rho and sound speed
 //                              of u_h at each vertex (2 padding values)
@@ -73,6 +75,9 @@ template <> struct Geo<float> {
 // are the negated values the other cell uses, bit for bit.
 template <typename Real> struct TraceStride { static constexpr int value = sizeof(Real) == 4 ? 4 : 8; };
 __host__ __device__ constexpr int trace_stride(int precision) { return precision == 0 ? 8 : 4; }
+// the exchange buffers (traces, vertex records, Hessians, edge records) are
+// used by the FP64 form only; the mixed form's passes read the states directly
+__host__ __device__ constexpr bool uses_exchange(int precision) { return precision == 0; }
 // per-edge OE record ej[ne][EJ_STRIDE]: beta, then sqrt(2 J) of the trapezoidal
 // jump sums J for q = rho, (m_n|m_t max | m1), (m2), E and j = 0..k (13 used)
 constexpr int EJ_STRIDE = 16;
@@ -275,9 +280,10 @@ __device__ __forceinline__ bool gt0(double x) { return __double_as_longlong(x) >
 __device__ __forceinline__ bool gt0(float x) { return x > 0.0f; }
 // exp(-x), x >= 0 (or NaN): small FP64 arguments, the usual case of the OE
 // damping away from discontinuities, take a 7-FMA Taylor polynomial
-// (dg_math.h); the rest, and FP32, the library exp
+// (dg_math.h); the rest the library exp; FP32 the fast intrinsic, whose
+// error (a few ulp) is far below the mixed form's FP32 arithmetic error
 __device__ __forceinline__ double exp_neg(double x) { return x <= EXP_NEG_SMALL_MAX ? exp_neg_small(x) : exp(-x); }
-__device__ __forceinline__ float exp_neg(float x) { return expf(-x); }
+__device__ __forceinline__ float exp_neg(float x) { return __expf(-x); }
 
 // x != 0 on the integer units (true for NaN, false for +0 and -0, as the comparison)
 __device__ __forceinline__ bool nonzero_bits(double x) { return (__double_as_longlong(x) << 1) != 0; }

@@ -50,7 +50,7 @@ void launch_fin_dev(const StageCtx &c);
 void launch_oe_bp(const StageCtx &c, const StateBuf &uh, const StateBuf &out, int do_oe, int do_bp, double c_out,
                   int stage);
 void launch_oe_bp_only(const StageCtx &c, const StateBuf &uh, const StateBuf &out, int do_oe, int do_bp,
-                       double c_out);
+                       double c_out, int end_of_step);
 void launch_fin_alpha(const StageCtx &c, int stage);
 void launch_step_begin(const StageCtx &c);
 void launch_set_active(const StageCtx &c, int active);
@@ -85,6 +85,8 @@ size_t stage_kernels_local_bytes(int k, int prec);
 
 // mesh size, device cell areas and their host-summed total (dg_api.cu)
 void mesh_view(const dg_mesh *mesh, int64_t *nt, const double **area, double *area_total);
+// the CUDA device that was current when the mesh was created (dg_api.cu)
+int mesh_device(const dg_mesh *mesh);
 // record a message for dg_last_error and return code (dg_api.cu)
 int32_t set_error(int32_t code, const char *msg);
 

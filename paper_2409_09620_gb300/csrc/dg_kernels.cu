@@ -181,9 +181,9 @@ static void stats_impl(cudaStream_t s, const MeshDev &m, const Phys &ph, StateDe
 template <int K, typename Real>
 static void oebp_impl(cudaStream_t s, const MeshDev &m, const Phys &ph, StateDev<Real> uh, StateDev<Real> out,
                       const void *ej, void *tr, double *pa, long long *pc, const Scalars *sc, int do_oe,
-                      int do_bp, double c_out) {
+                      int do_bp, double c_out, int end_of_step) {
   k_oe_bp<K, Real><<<nblocks(m.nt), TPB, 0, s>>>(m, ph, uh, out, (const Real *)ej, (Real *)tr, pa, pc, sc, do_oe,
-                                                 do_bp, c_out);
+                                                 do_bp, c_out, end_of_step);
 }
 
 #define DG_DISPATCH(K_, PREC_, CALL)                        \
@@ -237,10 +237,10 @@ void launch_stats(const StageCtx &c, const StateBuf &uh, double c_out) {
 
 // k_oe_bp: RIOE + limiter + traces, block maxima of the wave speed and counters
 void launch_oe_bp_only(const StageCtx &c, const StateBuf &uh, const StateBuf &out, int do_oe, int do_bp,
-                       double c_out) {
+                       double c_out, int end_of_step) {
   DG_DISPATCH(c.k, c.prec,
               (oebp_impl<KK, Real>(c.stream, c.mesh, c.phys, {uh.avg, (Real *)uh.hi}, {out.avg, (Real *)out.hi}, c.ej,
-                                   c.tr, c.part_alpha, c.part_cnt, c.sc, do_oe, do_bp, c_out)));
+                                   c.tr, c.part_alpha, c.part_cnt, c.sc, do_oe, do_bp, c_out, end_of_step)));
 }
 
 // alpha and counters; after stage 2 also t += dt (stage < 0: outside a step)
@@ -251,7 +251,7 @@ void launch_fin_alpha(const StageCtx &c, int stage) {
 
 void launch_oe_bp(const StageCtx &c, const StateBuf &uh, const StateBuf &out, int do_oe, int do_bp, double c_out,
                   int stage) {
-  launch_oe_bp_only(c, uh, out, do_oe, do_bp, c_out);
+  launch_oe_bp_only(c, uh, out, do_oe, do_bp, c_out, stage == 2);
   launch_fin_alpha(c, stage);
 }
 

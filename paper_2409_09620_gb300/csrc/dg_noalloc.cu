@@ -145,6 +145,8 @@ extern "C" int32_t dg_stats_noalloc(const dg_mesh *mesh, int32_t k, const double
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return set_error(DG_ECUDA, cudaGetErrorString(e));
   if (dev < 0 || dev >= NA_MAX_DEVICES) return set_error(DG_EINVAL, "dg_stats_noalloc: device id too large");
+  if (dev != mesh_device(mesh))
+    return set_error(DG_EINVAL, "dg_stats_noalloc: the current device is not the one that holds the mesh");
   double *scratch = nullptr;
   {
     // once per device, with that device current: the device address of the array

@@ -55,7 +55,8 @@ size_t solve_bytes(int64_t nt, int k, int prec) {
   const size_t nb = k == 1 ? 3 : 6, nq = k == 1 ? 2 : 3;
   const size_t mesh = 45 * 8 + 23 * 4 + 2 + 12 + 4 * 3 + 4 * 2;   // geometry (FP64 + FP32 copies), connectivity, edges
   const size_t state = 3 * (4 * 8 + rs * 4 * (nb - 1));
-  const size_t exch = rs * (3 * nq * trace_stride(prec) + 48 + 12 + 2 * 16);   // traces, vertex records, Hessians, ~1.5 edge records
+  // traces, vertex records, Hessians, ~1.5 edge records (FP64 form only)
+  const size_t exch = uses_exchange(prec) ? rs * (3 * nq * trace_stride(prec) + 48 + 12 + 2 * 16) : 0;
   const size_t part = 10 * 8 + 16;   // per 128-cell block, rounded up per cell below
   return (size_t)nt * (mesh + state + exch) + ((size_t)nt / 128 + 1) * part + 4096;
 }

@@ -21,13 +21,13 @@ namespace dg {
 // instantiations).  Higher occupancy hides the latency of the neighbour
 // gathers and of the FP64 pipe better than the few spilled registers cost.
 #ifndef RK_MINB_F
-#define RK_MINB_F 6
+#define RK_MINB_F 4
 #endif
 #ifndef STATS_MINB_F
 #define STATS_MINB_F 6
 #endif
 #ifndef OEBP_MINB_F
-#define OEBP_MINB_F 6
+#define OEBP_MINB_F 4
 #endif
 #ifndef RK_MINB_D
 #define RK_MINB_D 3
@@ -75,6 +75,19 @@ __device__ __forceinline__ void to_real(const double a[4], Real r[4]) {
 }
 __device__ __forceinline__ double reload_avg(const double *p) { return __ldcg(p); }
 
+// The mixed-precision form has its own tile functions without exchange
+// buffers (dg_stage_mixed.cuh); the generic tile functions hand FP32 work to
+// them.
+template <int K>
+__device__ __forceinline__ void rk_tile_mixed(const MeshDev &m, const Phys &ph, StateDev<float> v, StateDev<float> un,
+                                              StateDev<float> uh, double *part_sum, const Scalars *sc, double a,
+                                              double b, double c_in, int64_t tile);
+template <int K>
+__device__ __forceinline__ void oe_bp_tile_mixed(const MeshDev &m, const Phys &ph, StateDev<float> uh,
+                                                 StateDev<float> out, double *part_alpha, long long *part_cnt,
+                                                 const Scalars *sc, int do_oe, int do_bp, double c_out, int end_of_step,
+                                                 int64_t tile);
+
 // ==========================================================================
 // K1: u_h = a u_n + b (v + dt L(v))
 // ==========================================================================
@@ -85,6 +98,10 @@ __device__ __forceinline__ void rk_tile(const MeshDev &m, const Phys &ph, StateD
                                         Real *__restrict__ hso, double *part_sum,
                                         const Scalars *sc, double a, double b, double c_in,
                                         int64_t tile) {
+  if constexpr (sizeof(Real) == sizeof(float)) {
+    rk_tile_mixed<K>(m, ph, v, un, uh, part_sum, sc, a, b, c_in, tile);
+    return;
+  }
   constexpr int NB = Deg<K>::NB, NQ = Deg<K>::NQ, NV = Deg<K>::NV;
   const int64_t nt = m.nt;
   const int64_t Kc = tile * TPB + threadIdx.x;
@@ -454,6 +471,7 @@ template <int K, typename Real>
 __device__ __forceinline__ void edge_tile(const MeshDev &m, const Phys &ph, const Real *__restrict__ vdi,
                                           const Real *__restrict__ hsi, Real *__restrict__ ej,
                                           const Scalars *sc, double c_out, int64_t tile) {
+  if constexpr (sizeof(Real) == sizeof(float)) return;   // the mixed form forms its jumps in K3
   const int64_t nt = m.nt;
   const int64_t e0 = m.etile[tile], e1 = m.etile[tile + 1];
   const double t_out = sc->t + c_out * sc->dt;
@@ -724,187 +742,16 @@ __device__ __noinline__ void limit_mixed_fp64(const MeshDev &m, const Phys &ph, 
   *limited = cnt[0];
 }
 
-// --------------------------------------------------------------------------
-// BP limiter and traces of the mixed-precision form (FP32 modes, FP64 cell
-// averages).  Every point of the limiter set is first screened in FP32 with a
-// margin far above the FP32 evaluation error; a cell that passes is admissible
-// with theta = 1.  Other cells get the paper's theta (Sec. 4.4) in FP64, with
-// the targets raised by the rounding that storing the scaled modes in FP32
-// can cause; the stored state is then re-evaluated in FP64 at every point and,
-// if a bound still fails, the cell falls back to its (admissible) average.
-// --------------------------------------------------------------------------
-template <int K>
-__device__ __forceinline__ void limit_and_trace_mixed(const MeshDev &m, const Phys &ph, const double a0[4],
-                                                      float hi[4][Deg<K>::NB], const float nxs[3],
-                                                      const float nys[3], const int32_t cns[3], StateDev<float> out,
-                                                      float *tr, int64_t Kc, double t_out, int do_bp, double &amax,
-                                                      long long cnt[2]) {
-  constexpr int NB = Deg<K>::NB, NQ = Deg<K>::NQ, NE = 3 * NQ;
-  const int64_t nt = m.nt;
-  const float gamma = ph.gamma_f, gm1 = ph.gm1_f;
-  // the two extra points of the limiter set for the FP32 screen (P1: vertices
-  // v1, v2; P2: internal nodes, from the mesh's FP32 copy)
-  float px[2], py[2];
-  if (K == 1) {
-    const int v1 = m.limv[Kc], v2 = m.limv[nt + Kc];
-    px[0] = float(vert_xi(v1)); py[0] = float(vert_eta(v1)); px[1] = float(vert_xi(v2)); py[1] = float(vert_eta(v2));
-  } else {
-    px[0] = m.node_f[Kc]; py[0] = m.node_f[nt + Kc]; px[1] = m.node_f[2 * nt + Kc]; py[1] = m.node_f[3 * nt + Kc];
-  }
-  // FP32 deviations u - ubar at the edge Gauss points
-  float df[NE][4];
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int nu = 0; nu < NQ; ++nu) {
-      const double xi = edge_xi(i, gauss_s(NQ, nu)), eta = edge_eta(i, gauss_s(NQ, nu));
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        float sacc = 0.0f;
-#pragma unroll
-        for (int l = 1; l < NB; ++l) sacc = cfma(psi(l, xi, eta), hi[c][l], sacc);
-        df[i * NQ + nu][c] = sacc;
-      }
-    }
-  // the averages are unchanged by the limiter: store them now, take what is
-  // needed in FP64, and continue with FP32 copies (the rare FP64 branch
-  // reloads them)
-#pragma unroll
-  for (int c = 0; c < 4; ++c) out.avg[c * nt + Kc] = a0[c];
-  float a0f[4];
-  to_real(a0, a0f);
-  // admissibility of the average and eps1 = min(rho, 1e-13), eps2 =
-  // min(Ebar, 1e-13) of Sec. 4.4.  An FP32 screen settles the usual case
-  // without the FP64 division: rho > 2e-13 and rho Ebar = rho E - |m|^2 / 2 >
-  // 2e-13 rho with a margin (1e-5 relative) far above the FP32 rounding of the
-  // test imply rho > 1e-13 and Ebar > 1e-13 exactly, hence eps1 = eps2 = 1e-13.
-  // Anything else (tiny, non-finite, near the bounds) takes the FP64 path.
-  bool avg_ok;
-  float eps1, eps2;
-  {
-    const float q2 = fdot2(a0f[1], a0f[1], a0f[2], a0f[2]), pe = a0f[3] * a0f[0];
-    if (a0f[0] > 2e-13f && fmaf(-0.5f, q2, pe) > fdot2(2e-13f, a0f[0], 1e-5f, fmaf(0.5f, q2, fabsf(pe)))) {
-      avg_ok = true;
-      eps1 = eps2 = float(1e-13);
-    } else {
-      const double Ebar = int_energy(a0);
-      avg_ok = (a0[0] > 0.0) && (Ebar > 0.0);
-      eps1 = float(fmin(a0[0], 1e-13));
-      eps2 = float(fmin(Ebar, 1e-13));
-    }
-  }
-  bool lim64 = false;
-  if (do_bp) {
-    if (!avg_ok) {
-      cnt[1] = 1;
-    } else {
-      float S[4];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        S[c] = fabsf(a0f[c]);
-#pragma unroll
-        for (int l = 1; l < NB; ++l) S[c] += 4.0f * fabsf(hi[c][l]);   // |Psi_l| <= 4 on K
-      }
-      auto passes = [&](const float d[4]) -> bool {
-        const float r = a0f[0] + d[0];
-        if (!(r >= eps1 + 1e-5f * S[0])) return false;
-        const float m1 = a0f[1] + d[1], m2 = a0f[2] + d[2], E = a0f[3] + d[3];
-        const float ri = 1.0f / r;
-        const float q = fdot2(m1, m1, m2, m2) * ri;          // |m|^2 / rho
-        const float v = sqrtf(q * ri);                       // |v|
-        const float margin = fdot2(1e-5f, fmaf(v, S[1] + S[2], fmaf(v * v, S[0], S[3])), 1e-6f, fabsf(E) + q);
-        return E - 0.5f * q >= eps2 + margin;
-      };
-      bool ok = true;
-#pragma unroll
-      for (int p = 0; p < NE; ++p) ok = passes(df[p]) && ok;
-      float dx[NE + 2][4];
-      if (ph.decomp) {
-#pragma unroll
-        for (int p = 0; p < NE; ++p)
-#pragma unroll
-          for (int c = 0; c < 4; ++c) dx[p][c] = df[p][c];
-        zxs_extra_points<K, float, NE + 2>(dx);
-      } else {
-#pragma unroll
-        for (int p = 0; p < 2; ++p)
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            float sacc = 0.0f;
-#pragma unroll
-            for (int l = 1; l < NB; ++l) sacc = fmaf(psi_t<float>(l, px[p], py[p]), hi[c][l], sacc);
-            dx[NE + p][c] = sacc;
-          }
-      }
-#pragma unroll
-      for (int p = 0; p < 2; ++p) ok = passes(dx[NE + p]) && ok;
-      lim64 = !ok;
-    }
-  }
-  float ut[NE][4];
-  if (!lim64) {
-#pragma unroll
-    for (int c = 0; c < 4; ++c)
-#pragma unroll
-      for (int l = 1; l < NB; ++l) out.hi[(c * (NB - 1) + (l - 1)) * nt + Kc] = hi[c][l];
-#pragma unroll
-    for (int p = 0; p < NE; ++p)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) ut[p][c] = a0f[c] + df[p][c];
-  } else {
-    // FP64 theta (Sec. 4.4 Steps 1-2) out of line
-    double a0l[4];
-    float hl[4][NB], utl[NE][4];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      a0l[c] = reload_avg(out.avg + c * nt + Kc);
-#pragma unroll
-      for (int l = 0; l < NB; ++l) hl[c][l] = hi[c][l];
-    }
-    long long lim = 0;
-    limit_mixed_fp64<K>(m, ph, a0l, &hl[0][0], out, Kc, &utl[0][0], &lim);
-    if (lim) cnt[0] = 1;
-#pragma unroll
-    for (int p = 0; p < NE; ++p)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) ut[p][c] = utl[p][c];
-  }
-  // traces, F.n and wave speed at the edge Gauss points for the next stage
-  float amax32 = 0.0f;
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-#pragma unroll
-    for (int nu = 0; nu < NQ; ++nu) {
-      float f[4];
-      const float *u = ut[i * NQ + nu];
-      const float r = flux_speed(u, nxs[i], nys[i], gm1, gamma, f);
-      amax32 = (r > amax32 || r != r) ? r : amax32;
-      vstore<4>(tr + ((Kc * 3 + i) * NQ + nu) * 4, u);   // u only: k_rk recomputes F(u).n
-      if (cns[i] <= -3) {
-        double qx = 0.0, qy = 0.0;
-        if (cns[i] == -7) {
-          const double sg = gauss_s(NQ, nu);
-          const double xa = m.vxy[(2 * ((i + 1) % 3)) * nt + Kc], ya = m.vxy[(2 * ((i + 1) % 3) + 1) * nt + Kc];
-          const double xb = m.vxy[(2 * ((i + 2) % 3)) * nt + Kc], yb = m.vxy[(2 * ((i + 2) % 3) + 1) * nt + Kc];
-          qx = xa + (xb - xa) * sg;
-          qy = ya + (yb - ya) * sg;
-        }
-        float up[4];
-        ghost_state(-cns[i], u, nxs[i], nys[i], qx, qy, t_out, ph, up);
-        const float rg = wave_speed(up, nxs[i], nys[i], gamma);
-        amax32 = (rg > amax32 || rg != rg) ? rg : amax32;
-      }
-    }
-  }
-  amax = max_nn(amax, double(amax32));
-}
-
 template <int K, typename Real>
 __device__ __forceinline__ void oe_bp_tile(const MeshDev &m, const Phys &ph, StateDev<Real> uh, StateDev<Real> out,
                                            const Real *__restrict__ ej,
                                            Real *__restrict__ tr, double *part_alpha,
                                            long long *part_cnt, const Scalars *sc,
-                                           int do_oe, int do_bp, double c_out, int64_t tile) {
+                                           int do_oe, int do_bp, double c_out, int end_of_step, int64_t tile) {
+  if constexpr (sizeof(Real) == sizeof(float)) {
+    oe_bp_tile_mixed<K>(m, ph, uh, out, part_alpha, part_cnt, sc, do_oe, do_bp, c_out, end_of_step, tile);
+    return;
+  }
   constexpr int NB = Deg<K>::NB, NQ = Deg<K>::NQ;
   constexpr int NE = 3 * NQ;          // edge Gauss points
   const int64_t nt = m.nt;
@@ -912,7 +759,10 @@ __device__ __forceinline__ void oe_bp_tile(const MeshDev &m, const Phys &ph, Sta
   double amax = 0.0;
   long long cnt[2] = {0, 0};
   if (Kc < nt) {
-    const double dt = sc->dt, t_out = sc->t + c_out * sc->dt;
+    // exterior states for the next stage's alpha at the time of the stage
+    // result: t + c_out dt, and after the last stage of a step clamped to
+    // the end time, the end time itself (the next step starts there)
+    const double dt = sc->dt, t_out = end_of_step && sc->pad ? sc->t_end : sc->t + c_out * sc->dt;
     const Real gamma = phys_gamma<Real>(ph);
     double a0[4];
     Real hi[4][NB];
@@ -1080,13 +930,32 @@ __device__ __forceinline__ void oe_bp_tile(const MeshDev &m, const Phys &ph, Sta
   #pragma unroll
       for (int c = 0; c < 4; ++c) out.avg[c * nt + Kc] = a0[c];
       if (th_r < 1.0 || th_a < 1.0) {   // rare: the cell is limited
+        // store the scaled modes, and take the traces below from the stored
+        // modes, so that a run resumed from the stored state (dg_set_state)
+        // sees the same traces bit for bit
   #pragma unroll
         for (int c = 0; c < 4; ++c) {
           const double th = c == 0 ? th_r : th_a;
   #pragma unroll
-          for (int l = 1; l < NB; ++l)
-            out.hi[(c * (NB - 1) + (l - 1)) * nt + Kc] = th < 1.0 ? Real(th * double(hi[c][l])) : hi[c][l];
+          for (int l = 1; l < NB; ++l) {
+            hi[c][l] = th < 1.0 ? Real(th * double(hi[c][l])) : hi[c][l];
+            out.hi[(c * (NB - 1) + (l - 1)) * nt + Kc] = hi[c][l];
+          }
         }
+  #pragma unroll
+        for (int i = 0; i < 3; ++i)
+  #pragma unroll
+          for (int nu = 0; nu < NQ; ++nu) {
+            const double xi = edge_xi(i, gauss_s(NQ, nu)), eta = edge_eta(i, gauss_s(NQ, nu));
+  #pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              double s = 0.0;
+  #pragma unroll
+              for (int l = 1; l < NB; ++l) s = cfma(psi(l, xi, eta), double(hi[c][l]), s);
+              dev[i * NQ + nu][c] = s;
+            }
+          }
+        th_r = th_a = 1.0;
       } else {
   #pragma unroll
         for (int c = 0; c < 4; ++c)
@@ -1127,8 +996,6 @@ __device__ __forceinline__ void oe_bp_tile(const MeshDev &m, const Phys &ph, Sta
           }
         }
       }
-    } else {
-      limit_and_trace_mixed<K>(m, ph, a0, hi, nxs, nys, cns, out, tr, Kc, t_out, do_bp, amax, cnt);
     }
   }
   double av[1] = {amax};
@@ -1154,9 +1021,11 @@ template <int K, typename Real>
 __global__ void __launch_bounds__(TPB, sizeof(Real) == 4 ? OEBP_MINB_F : OEBP_MINB_D)
     k_oe_bp(MeshDev m, Phys ph, StateDev<Real> uh, StateDev<Real> out, const Real *__restrict__ ej,
             Real *__restrict__ tr, double *part_alpha, long long *part_cnt, const Scalars *sc, int do_oe,
-            int do_bp, double c_out) {
+            int do_bp, double c_out, int end_of_step) {
   if (!sc->active) return;
-  oe_bp_tile<K, Real>(m, ph, uh, out, ej, tr, part_alpha, part_cnt, sc, do_oe, do_bp, c_out, blockIdx.x);
+  oe_bp_tile<K, Real>(m, ph, uh, out, ej, tr, part_alpha, part_cnt, sc, do_oe, do_bp, c_out, end_of_step, blockIdx.x);
 }
 
 }  // namespace dg
+
+#include "dg_stage_mixed.cuh"
