@@ -25,9 +25,15 @@
  *  - alpha of the LF flux is the maximum wave speed over the edge Gauss
  *    points of the stage input (eq. 1250), boundary ghost states included;
  *    dt is fixed per step from the first stage's alpha (Sec. 5);
- *  - the OE jumps on a boundary edge are taken against the same ghost as the
- *    flux: the mirror polynomial on a reflecting wall, the own polynomial on
- *    a transmissive edge, a constant state on a Dirichlet / shock edge;
+ *  - the exterior state of a transmissive (outflow) edge is the cell's own
+ *    average, a constant: in the flux, in alpha and in the OE jumps (zero
+ *    exterior derivatives); the interior trace itself would add no
+ *    dissipation at the edge, and gas at rest next to such an edge then
+ *    amplifies round-off;
+ *  - the OE jumps on a boundary edge are taken against the same exterior
+ *    state as the flux: the mirror polynomial on a reflecting wall, the cell
+ *    average on a transmissive edge, a constant state on a Dirichlet / shock
+ *    edge;
  *  - the wave speed R(u, n) is +inf for rho <= 0 and uses max(p, 0) in the
  *    sound speed (it is evaluated at vertices that the limiter does not
  *    control); a term beta/h * delta with delta = 0 contributes 0;
@@ -217,9 +223,10 @@ static double shock_position(const or_config *cf, double y, double t) {
   return cf->shock_x0 + y / tan(cf->shock_angle) + cf->shock_speed * t / sin(cf->shock_angle);
 }
 
-/* exterior state at a boundary point from the interior state */
-static void ghost_state(const or_config *cf, int tag, const double uin[4], const double n[2],
-                        double x, double y, double t, double out[4]) {
+/* exterior state at a boundary point from the interior state uin and the
+ * cell average ubar */
+static void ghost_state(const or_config *cf, int tag, const double uin[4], const double ubar[4],
+                        const double n[2], double x, double y, double t, double out[4]) {
   if (tag == OR_BC_REFLECT) {
     double mn = uin[1] * n[0] + uin[2] * n[1];
     out[0] = uin[0];
@@ -231,9 +238,14 @@ static void ghost_state(const or_config *cf, int tag, const double uin[4], const
   } else if (tag == OR_BC_SHOCK) {
     int s = x < shock_position(cf, y, t) ? cf->shock_post : cf->shock_pre;
     for (int c = 0; c < 4; ++c) out[c] = cf->bc_state[s][c];
-  } else { /* transmissive */
-    for (int c = 0; c < 4; ++c) out[c] = uin[c];
+  } else { /* transmissive: the cell average */
+    for (int c = 0; c < 4; ++c) out[c] = ubar[c];
   }
+}
+
+/* cell average of cell K (mode 0) */
+static void cell_average(const or_mesh *m, int k, const double *u, int64_t K, double ubar[4]) {
+  for (int c = 0; c < 4; ++c) ubar[c] = coef(u, m->nt, nbasis(k), c, 0, K);
 }
 
 /* exterior trace at the physical point (x, y) of edge i of cell K */
@@ -246,7 +258,9 @@ static void exterior_trace(const or_mesh *m, const or_config *cf, const double *
     cell_geo(m, nb_cell, &gn);
     eval_at(m, cf->k, u, nb_cell, &gn, x + m->shift[6 * K + 2 * i], y + m->shift[6 * K + 2 * i + 1], uex);
   } else {
-    ghost_state(cf, m->bc[3 * K + i], uin, n, x, y, t, uex);
+    double ubar[4];
+    cell_average(m, cf->k, u, K, ubar);
+    ghost_state(cf, m->bc[3 * K + i], uin, ubar, n, x, y, t, uex);
   }
 }
 
@@ -503,8 +517,9 @@ static double cell_alpha(const or_mesh *m, const or_config *cf, const double *u,
       double r = wave_speed(uin, g.n[i], cf->gamma);
       if (r > best || r != r) best = r;
       if (m->nbr[3 * K + i] < 0) {
-        double uex[4];
-        ghost_state(cf, m->bc[3 * K + i], uin, g.n[i], x, y, t, uex);
+        double uex[4], ubar[4];
+        cell_average(m, cf->k, u, K, ubar);
+        ghost_state(cf, m->bc[3 * K + i], uin, ubar, g.n[i], x, y, t, uex);
         double re = wave_speed(uex, g.n[i], cf->gamma);
         if (re > best || re != re) best = re;
       }
@@ -687,8 +702,8 @@ int or_stats(const or_mesh *m, const or_config *cf, const double *u, double *sta
 /* (oe:sysdelta2), (RIOESys:CoefM/Coef1/Coef2) with the trapezoidal rule     */
 /* ------------------------------------------------------------------------ */
 /* ghost derivatives on a boundary edge (val, grad, hess of the 4 components) */
-static void ghost_derivs(const or_config *cf, int tag, const double n[2], double x, double y, double t,
-                         const double val[4], const double grad[4][2], const double hess[4][3],
+static void ghost_derivs(const or_config *cf, int tag, const double ubar[4], const double n[2], double x,
+                         double y, double t, const double val[4], const double grad[4][2], const double hess[4][3],
                          double gv[4], double gg[4][2], double gh[4][3]) {
   if (tag == OR_BC_REFLECT) {
     /* mirror polynomial: q_g(x) = q(Rx) for rho, E; m_g(x) = R m(Rx); R = I - 2 n n^T */
@@ -732,19 +747,13 @@ static void ghost_derivs(const or_config *cf, int tag, const double n[2], double
       gh[1 + a][1] = R[a][0] * RHR[1][0][1] + R[a][1] * RHR[2][0][1];
       gh[1 + a][2] = R[a][0] * RHR[1][1][1] + R[a][1] * RHR[2][1][1];
     }
-  } else if ((tag >= OR_BC_DIRICHLET0 && tag < OR_BC_DIRICHLET0 + 4) || tag == OR_BC_SHOCK) {
+  } else { /* constant exterior states: Dirichlet, moving shock, the transmissive cell average */
     double st[4];
-    ghost_state(cf, tag, val, n, x, y, t, st);
+    ghost_state(cf, tag, val, ubar, n, x, y, t, st);
     for (int c = 0; c < 4; ++c) {
       gv[c] = st[c];
       gg[c][0] = gg[c][1] = 0.0;
       gh[c][0] = gh[c][1] = gh[c][2] = 0.0;
-    }
-  } else { /* transmissive: the own polynomial, no jump */
-    for (int c = 0; c < 4; ++c) {
-      gv[c] = val[c];
-      gg[c][0] = grad[c][0]; gg[c][1] = grad[c][1];
-      gh[c][0] = hess[c][0]; gh[c][1] = hess[c][1]; gh[c][2] = hess[c][2];
     }
   }
 }
@@ -805,7 +814,9 @@ static void cell_sigma(const or_mesh *m, const or_config *cf, const double *u, c
         cell_geo(m, nbc, &gn);
         eval_derivs(m, k, u, nbc, &gn, x + m->shift[6 * K + 2 * i], y + m->shift[6 * K + 2 * i + 1], ov, og, oh);
       } else {
-        ghost_derivs(cf, m->bc[3 * K + i], n, x, y, t, val, grad, hess, ov, og, oh);
+        double ubar[4];
+        cell_average(m, k, u, K, ubar);
+        ghost_derivs(cf, m->bc[3 * K + i], ubar, n, x, y, t, val, grad, hess, ov, og, oh);
       }
       /* beta_K^(i): max spectral radius over both sides at both endpoints */
       double r1 = wave_speed(val, n, cf->gamma), r2 = wave_speed(ov, n, cf->gamma);

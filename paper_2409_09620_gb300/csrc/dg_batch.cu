@@ -146,10 +146,12 @@ __device__ __forceinline__ void phase_stats(const SolveDev *__restrict__ sv, con
     for (int64_t t = it.first_tile; t < it.first_tile + it.ntiles; ++t) {
       if (S.k == 1) {
         stats_tile<1, Real>(S.mesh, uh, S.part_dev, S.sc, t);
-        edge_tile<1, Real>(S.mesh, S.ph, (const Real *)S.vd, (const Real *)S.hs, (Real *)S.ej, S.sc, c_out, t);
+        edge_tile<1, Real>(S.mesh, S.ph, uh.avg, (const Real *)S.vd, (const Real *)S.hs, (Real *)S.ej, S.sc, c_out,
+                           t);
       } else {
         stats_tile<2, Real>(S.mesh, uh, S.part_dev, S.sc, t);
-        edge_tile<2, Real>(S.mesh, S.ph, (const Real *)S.vd, (const Real *)S.hs, (Real *)S.ej, S.sc, c_out, t);
+        edge_tile<2, Real>(S.mesh, S.ph, uh.avg, (const Real *)S.vd, (const Real *)S.hs, (Real *)S.ej, S.sc, c_out,
+                           t);
       }
       finish_deviations(S.part_dev, S.fin, t, S.ntiles, S.sc, S.oe == 2);
     }
@@ -247,6 +249,10 @@ struct BatchCore {
   BarrierState *d_bar = nullptr;
   unsigned long long bar_timeout_ns = BARRIER_TIMEOUT_NS;
   unsigned bar_extra = 0;
+  // the server's core picks the chunk size from the cells in the batch: the
+  // largest power of two (up to 8 tiles) that still gives every resident
+  // block of the grid two chunks, so a few small solves spread over the GPU
+  bool auto_chunk = false;
   int nwork = 0, grid = 0, cpb = 4 * TPB, blocks_per_sm = 0, num_sms = 0, form = 3;
   int occ_fused = 0, occ_phase[3] = {0, 0, 0}, grid_phase[3] = {0, 0, 0};
   cudaGraphExec_t exec = nullptr;
@@ -367,6 +373,14 @@ struct BatchCore {
     if (!host_sv.empty() &&
         cudaMemcpy(d_sv, host_sv.data(), sizeof(SolveDev) * host_sv.size(), cudaMemcpyHostToDevice) != cudaSuccess)
       return set_error(DG_ECUDA, "solve table upload");
+    if (auto_chunk) {
+      int64_t tiles = 0;
+      for (const SolveDev &d : host_sv) tiles += d.ntiles;
+      const int64_t resident = (int64_t)num_sms * std::max(1, max_blocks_per_sm(form));
+      int tpw = 1;
+      while (tpw < 8 && tiles / (2 * tpw) >= 2 * resident) tpw *= 2;
+      cpb = tpw * TPB;
+    }
     return set_shape(cpb, blocks_per_sm, form);
   }
 
@@ -682,6 +696,7 @@ int32_t batch_core_new(int precision, cudaStream_t stream, BatchCore **out) {
   if (!c) return set_error(DG_ENOMEM, "host allocation failed");
   int32_t rc = c->init(precision, stream);
   if (rc != DG_OK) { delete c; return rc; }
+  c->auto_chunk = true;
   *out = c;
   return DG_OK;
 }

@@ -252,7 +252,7 @@ __device__ __forceinline__ T fdot2(T a, T b, T c, T d) { return fma(a, b, c * d)
 template <typename T>
 __device__ __forceinline__ T flux_dir(const T u[4], T dx, T dy, T gm1, T f[4]) {
   const T ri = T(1) / u[0];
-  const T p = gm1 * (u[3] - T(0.5) * fdot2(u[1], u[1], u[2], u[2]) * ri);
+  const T p = gm1 * fma(T(-0.5) * fdot2(u[1], u[1], u[2], u[2]), ri, u[3]);
   const T md = fdot2(u[1], dx, u[2], dy);
   const T vd = md * ri;
   f[0] = md;
@@ -266,7 +266,7 @@ __device__ __forceinline__ T flux_dir(const T u[4], T dx, T dy, T gm1, T f[4]) {
 template <typename T>
 __device__ __forceinline__ void flux_dir2(const T u[4], T d1x, T d1y, T d2x, T d2y, T gm1, T f1[4], T f2[4]) {
   const T ri = T(1) / u[0];
-  const T p = gm1 * (u[3] - T(0.5) * fdot2(u[1], u[1], u[2], u[2]) * ri);
+  const T p = gm1 * fma(T(-0.5) * fdot2(u[1], u[1], u[2], u[2]), ri, u[3]);
   const T ep = u[3] + p;
   const T m1 = fdot2(u[1], d1x, u[2], d1y), v1 = m1 * ri;
   const T m2 = fdot2(u[1], d2x, u[2], d2y), v2 = m2 * ri;
@@ -292,7 +292,7 @@ __device__ __forceinline__ bool nonzero_bits(float x) { return (__float_as_int(x
 // F(u) . n and the spectral radius |v.n| + c (+inf for rho <= 0) with one reciprocal
 template <typename T>
 __device__ __forceinline__ T flux_speed_ri(const T u[4], T ri, T nx, T ny, T gm1, T gamma, T f[4]) {
-  const T p = gm1 * (u[3] - T(0.5) * fdot2(u[1], u[1], u[2], u[2]) * ri);
+  const T p = gm1 * fma(T(-0.5) * fdot2(u[1], u[1], u[2], u[2]), ri, u[3]);
   const T mn = fdot2(u[1], nx, u[2], ny);
   const T vn = mn * ri;
   f[0] = mn;
@@ -342,7 +342,7 @@ template <typename T>
 __device__ __forceinline__ T wave_speed(const T u[4], T nx, T ny, T gamma) {
   if (!gt0(u[0])) return T(INFINITY);
   const T ri = T(1) / u[0];
-  T p = (gamma - T(1)) * (u[3] - T(0.5) * fdot2(u[1], u[1], u[2], u[2]) * ri);
+  T p = (gamma - T(1)) * fma(T(-0.5) * fdot2(u[1], u[1], u[2], u[2]), ri, u[3]);
   p = gt0(p) ? p : T(0);
   return fma(fabs(fdot2(u[1], nx, u[2], ny)), ri, sqrt(gamma * p * ri));
 }
@@ -351,15 +351,16 @@ __device__ __forceinline__ double int_energy(const double u[4]) {
   return u[3] - 0.5 * fdot2(u[1], u[1], u[2], u[2]) / u[0];
 }
 
-// exterior state of a boundary edge (tag > 0) at physical point (px, py), time t
+// exterior state of a boundary edge (tag > 0) at physical point (px, py),
+// time t, from the interior trace um and the cell average avg
 template <typename T>
-__device__ __forceinline__ void ghost_state(int tag, const T um[4], T nx, T ny, double px, double py, double t,
-                                            const Phys &ph, T up[4]) {
-  if (tag == 1) {                       // reflecting wall
-    const T mn = fdot2(um[1], nx, um[2], ny);
+__device__ __forceinline__ void ghost_state(int tag, const T um[4], const T avg[4], T nx, T ny, double px,
+                                            double py, double t, const Phys &ph, T up[4]) {
+  if (tag == 1) {                       // reflecting wall: m - 2 (m . n) n, the fused product fixed
+    const T mn2 = T(-2) * fdot2(um[1], nx, um[2], ny);
     up[0] = um[0];
-    up[1] = um[1] - T(2) * mn * nx;
-    up[2] = um[2] - T(2) * mn * ny;
+    up[1] = fma(mn2, nx, um[1]);
+    up[2] = fma(mn2, ny, um[2]);
     up[3] = um[3];
   } else if (tag >= 3 && tag <= 6) {    // constant state
 #pragma unroll
@@ -369,9 +370,9 @@ __device__ __forceinline__ void ghost_state(int tag, const T um[4], T nx, T ny, 
     const int s = px < xs ? ph.shock_post : ph.shock_pre;
 #pragma unroll
     for (int c = 0; c < 4; ++c) up[c] = T(ph.bc[s][c]);
-  } else {                              // transmissive
+  } else {                              // transmissive: the cell average (a constant state)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) up[c] = um[c];
+    for (int c = 0; c < 4; ++c) up[c] = avg[c];
   }
 }
 

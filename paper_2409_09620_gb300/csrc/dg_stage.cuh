@@ -107,7 +107,7 @@ __device__ __forceinline__ void rk_tile(const MeshDev &m, const Phys &ph, StateD
   const int64_t Kc = tile * TPB + threadIdx.x;
   double mass[4] = {0.0, 0.0, 0.0, 0.0};
   if (Kc < nt) {
-    const double dt = sc->dt, alpha_d = sc->alpha, t_in = sc->t + c_in * sc->dt;
+    const double dt = sc->dt, alpha_d = sc->alpha, t_in = fma(c_in, sc->dt, sc->t);
     const Real alpha = Real(alpha_d), gm1 = phys_gm1<Real>(ph);
     const double area = m.area[Kc];
     const Real *gj = Geo<Real>::jinv(m);
@@ -185,23 +185,18 @@ __device__ __forceinline__ void rk_tile(const MeshDev &m, const Phys &ph, StateD
             const double s = gauss_s(NQ, nu);
             const double xa = m.vxy[(2 * ((i + 1) % 3)) * nt + Kc], ya = m.vxy[(2 * ((i + 1) % 3) + 1) * nt + Kc];
             const double xb = m.vxy[(2 * ((i + 2) % 3)) * nt + Kc], yb = m.vxy[(2 * ((i + 2) % 3) + 1) * nt + Kc];
-            px = xa + (xb - xa) * s;
-            py = ya + (yb - ya) * s;
+            px = fma(xb - xa, s, xa);
+            py = fma(yb - ya, s, ya);
           }
-          ghost_state(-cn, um, nx, ny, px, py, t_in, ph, up);
-          if (cn == -2) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) fp[q] = fm[q];
-          } else {
-            flux_dir(up, nx, ny, gm1, fp);
-          }
+          ghost_state(-cn, um, v0r, nx, ny, px, py, t_in, ph, up);
+          flux_dir(up, nx, ny, gm1, fp);
         }
         // l_i w_nu / 2: the 1/2 of the LF flux rides on the weight (a power of
         // two, so the products are bitwise those of scaling the flux)
         const Real lw = li * Real(0.5 * gauss_w(NQ, nu));
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-          const Real fh = fm[c] + fp[c] - alpha * (up[c] - um[c]);
+          const Real fh = fma(-alpha, up[c] - um[c], fm[c] + fp[c]);
           const Real tv = lw * fh;
           if constexpr (sizeof(Real) == sizeof(double)) {
             acc0[c] -= double(tv);
@@ -252,7 +247,7 @@ __device__ __forceinline__ void rk_tile(const MeshDev &m, const Phys &ph, StateD
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         const double v0c = sizeof(Real) == sizeof(double) ? v0[c] : reload_avg(v.avg + c * nt + Kc);
-        if constexpr (FIRST) h0[c] = v0c + dta * acc0[c];
+        if constexpr (FIRST) h0[c] = fma(dta, acc0[c], v0c);
         else h0[c] = fdot2(a, un0[c], b, fma(dta, acc0[c], v0c));
         uh.avg[c * nt + Kc] = h0[c];
         mass[c] = area * h0[c];
@@ -323,7 +318,7 @@ __device__ __forceinline__ void rk_tile(const MeshDev &m, const Phys &ph, StateD
       Real ri = Real(0), cs = Real(INFINITY);
       if (gt0(val4[0])) {
         ri = Real(1) / val4[0];
-        Real p = gm1 * (val4[3] - Real(0.5) * fdot2(val4[1], val4[1], val4[2], val4[2]) * ri);
+        Real p = gm1 * fma(Real(-0.5) * fdot2(val4[1], val4[1], val4[2], val4[2]), ri, val4[3]);
         p = gt0(p) ? p : Real(0);
         cs = sqrt(gamma * p * ri);
       }
@@ -403,11 +398,14 @@ __device__ __forceinline__ void stats_tile(const MeshDev &m, StateDev<Real> uh, 
 // exterior vertex data of a boundary edge: value, gradient (x, y) and Hessian (xx, xy, yy)
 template <typename Real>
 __device__ __forceinline__ void ghost_vertex(int tag, const Real val[4], const Real grd[8], const Real hes[12],
-                                             Real nx, Real ny, double px, double py, double t, const Phys &ph,
-                                             Real ov[4], Real og[8], Real oh[12]) {
+                                             const Real avg[4], Real nx, Real ny, double px, double py, double t,
+                                             const Phys &ph, Real ov[4], Real og[8], Real oh[12]) {
   if (tag == 1) {
     // mirror polynomial: q(Rx) for rho, E and R m(Rx) for the momentum, R = I - 2 n n^T
-    const Real R00 = Real(1) - Real(2) * nx * nx, R01 = -Real(2) * nx * ny, R11 = Real(1) - Real(2) * ny * ny;
+    // with the fused products fixed (left to the compiler, the fusion could
+    // differ between the kernels that inline this, and a batch would not
+    // reproduce its solves bit for bit)
+    const Real R00 = fma(Real(-2) * nx, nx, Real(1)), R01 = Real(-2) * nx * ny, R11 = fma(Real(-2) * ny, ny, Real(1));
     Real RHR[4][3];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
@@ -439,22 +437,15 @@ __device__ __forceinline__ void ghost_vertex(int tag, const Real val[4], const R
       oh[3 + r] = fdot2(R00, RHR[1][r], R01, RHR[2][r]);
       oh[6 + r] = fdot2(R01, RHR[1][r], R11, RHR[2][r]);
     }
-  } else if (tag >= 3) {   // constant exterior state: no derivatives
+  } else {   // constant exterior states (Dirichlet, moving shock, the transmissive cell average): no derivatives
     Real st[4];
-    ghost_state(tag, val, nx, ny, px, py, t, ph, st);
+    ghost_state(tag, val, avg, nx, ny, px, py, t, ph, st);
 #pragma unroll
     for (int c = 0; c < 4; ++c) ov[c] = st[c];
 #pragma unroll
     for (int q = 0; q < 8; ++q) og[q] = Real(0);
 #pragma unroll
     for (int q = 0; q < 12; ++q) oh[q] = Real(0);
-  } else {                 // transmissive: the own polynomial
-#pragma unroll
-    for (int c = 0; c < 4; ++c) ov[c] = val[c];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) og[q] = grd[q];
-#pragma unroll
-    for (int q = 0; q < 12; ++q) oh[q] = hes[q];
   }
 }
 
@@ -468,13 +459,13 @@ __device__ __forceinline__ void ghost_vertex(int tag, const Real val[4], const R
 // Edges [etile[tile], etile[tile + 1]) are processed in chunks of TPB.
 // --------------------------------------------------------------------------
 template <int K, typename Real>
-__device__ __forceinline__ void edge_tile(const MeshDev &m, const Phys &ph, const Real *__restrict__ vdi,
-                                          const Real *__restrict__ hsi, Real *__restrict__ ej,
-                                          const Scalars *sc, double c_out, int64_t tile) {
+__device__ __forceinline__ void edge_tile(const MeshDev &m, const Phys &ph, const double *__restrict__ avg,
+                                          const Real *__restrict__ vdi, const Real *__restrict__ hsi,
+                                          Real *__restrict__ ej, const Scalars *sc, double c_out, int64_t tile) {
   if constexpr (sizeof(Real) == sizeof(float)) return;   // the mixed form forms its jumps in K3
   const int64_t nt = m.nt;
   const int64_t e0 = m.etile[tile], e1 = m.etile[tile + 1];
-  const double t_out = sc->t + c_out * sc->dt;
+  const double t_out = fma(c_out, sc->dt, sc->t);
   const Real gamma = phys_gamma<Real>(ph);
   const int cw = ph.oe == 2;
   for (int64_t e = e0 + threadIdx.x; e < e1; e += TPB) {
@@ -527,9 +518,12 @@ __device__ __forceinline__ void edge_tile(const MeshDev &m, const Phys &ph, cons
       } else {
         double px = 0.0, py = 0.0;
         if (cn == -7) { px = m.vxy[(2 * ov) * nt + Kc]; py = m.vxy[(2 * ov + 1) * nt + Kc]; }
-        ghost_vertex(-cn, val, grd, hme, nx, ny, px, py, t_out, ph, xv, xg, xh);
-        // a mirror or copied state has the same spectral radius
-        r_oth = cn >= -2 ? r_own : wave_speed(xv, nx, ny, gamma);
+        Real ab[4];   // the cell average (the exterior state of a transmissive edge)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) ab[c] = Real(avg[c * nt + Kc]);
+        ghost_vertex(-cn, val, grd, hme, ab, nx, ny, px, py, t_out, ph, xv, xg, xh);
+        // a mirror state has the same spectral radius
+        r_oth = cn == -1 ? r_own : wave_speed(xv, nx, ny, gamma);
       }
       beta = max_nn(beta, max_nn(r_own, r_oth));
       // the Hessians of P2 polynomials (and of every ghost) are constant, so
@@ -658,19 +652,19 @@ __device__ __noinline__ void limit_mixed_fp64(const MeshDev &m, const Phys &ph, 
 #pragma unroll
     for (int p = 0; p < NE + 2; ++p) rmin = fmin(rmin, a0[0] + d[p][0]);
     const double eps1 = fmin(a0[0], 1e-13);
-    const double tgt1 = fmin(a0[0], eps1 + 2.0 * r22 * Sa[0]);
+    const double tgt1 = fmin(a0[0], fma(2.0 * r22, Sa[0], eps1));
     const double th1 = rmin < tgt1 ? (a0[0] - tgt1) / (a0[0] - rmin) : 1.0;
     double emin = INFINITY, vmax2 = 0.0;
 #pragma unroll
     for (int p = 0; p < NE + 2; ++p) {
-      const double w0 = a0[0] + th1 * d[p][0], w1 = a0[1] + d[p][1], w2 = a0[2] + d[p][2], w3 = a0[3] + d[p][3];
+      const double w0 = fma(th1, d[p][0], a0[0]), w1 = a0[1] + d[p][1], w2 = a0[2] + d[p][2], w3 = a0[3] + d[p][3];
       const double q = fdot2(w1, w1, w2, w2);
       vmax2 = fmax(vmax2, q / (w0 * w0));
       emin = fmin(emin, w3 - 0.5 * q / w0);
     }
     const double RE = r22 * fma(sqrt(vmax2), Sa[1] + Sa[2], fma(vmax2 * th1, Sa[0], Sa[3]));
     const double eps2 = fmin(Ebar, 1e-13);
-    const double tgt2 = fmin(Ebar, eps2 + 2.0 * RE);
+    const double tgt2 = fmin(Ebar, fma(2.0, RE, eps2));
     const double th2 = emin < tgt2 ? (Ebar - tgt2) / (Ebar - emin) : 1.0;
     float hs[4][NB];
 #pragma unroll
@@ -762,7 +756,7 @@ __device__ __forceinline__ void oe_bp_tile(const MeshDev &m, const Phys &ph, Sta
     // exterior states for the next stage's alpha at the time of the stage
     // result: t + c_out dt, and after the last stage of a step clamped to
     // the end time, the end time itself (the next step starts there)
-    const double dt = sc->dt, t_out = end_of_step && sc->pad ? sc->t_end : sc->t + c_out * sc->dt;
+    const double dt = sc->dt, t_out = end_of_step && sc->pad ? sc->t_end : fma(c_out, sc->dt, sc->t);
     const Real gamma = phys_gamma<Real>(ph);
     double a0[4];
     Real hi[4][NB];
@@ -914,10 +908,10 @@ __device__ __forceinline__ void oe_bp_tile(const MeshDev &m, const Phys &ph, Sta
           double emin = INFINITY;
   #pragma unroll
           for (int p = 0; p < NE + 2; ++p) {
-            const double w0 = a0[0] + th1 * dev[p][0], w1 = a0[1] + dev[p][1], w2 = a0[2] + dev[p][2],
+            const double w0 = fma(th1, dev[p][0], a0[0]), w1 = a0[1] + dev[p][1], w2 = a0[2] + dev[p][2],
                          w3 = a0[3] + dev[p][3];
             const double q = 0.5 * fdot2(w1, w1, w2, w2);
-            if (!(w0 > 0.0) || w3 * w0 - q < eps2 * w0) emin = fmin(emin, w3 - q / w0);
+            if (!(w0 > 0.0) || fma(w3, w0, -q) < eps2 * w0) emin = fmin(emin, w3 - q / w0);
           }
           double th2 = 1.0;
           if (emin < eps2) th2 = (Ebar - eps2) / (Ebar - emin);
@@ -967,7 +961,7 @@ __device__ __forceinline__ void oe_bp_tile(const MeshDev &m, const Phys &ph, Sta
       const Real gm1 = phys_gm1<Real>(ph);
       double rho_t[NE], ri_t[NE];
   #pragma unroll
-      for (int p = 0; p < NE; ++p) rho_t[p] = a0[0] + th_r * dev[p][0];
+      for (int p = 0; p < NE; ++p) rho_t[p] = a0[0] + dev[p][0];   // theta is folded into dev above
       batch_reciprocal<NE>(rho_t, ri_t);
   #pragma unroll
       for (int i = 0; i < 3; ++i) {
@@ -975,23 +969,25 @@ __device__ __forceinline__ void oe_bp_tile(const MeshDev &m, const Phys &ph, Sta
         for (int nu = 0; nu < NQ; ++nu) {
           Real u[4], f[4];
   #pragma unroll
-          for (int c = 0; c < 4; ++c) u[c] = Real(a0[c] + (c == 0 ? th_r : th_a) * dev[i * NQ + nu][c]);
+          for (int c = 0; c < 4; ++c) u[c] = Real(a0[c] + dev[i * NQ + nu][c]);
           amax = max_nn(amax, double(flux_speed_ri(u, ri_t[i * NQ + nu], nxs[i], nys[i], gm1, gamma, f)));
           Real o8[8];
   #pragma unroll
           for (int q = 0; q < 4; ++q) { o8[q] = u[q]; o8[4 + q] = f[q]; }
           vstore<8>(tr + ((Kc * 3 + i) * NQ + nu) * 8, o8);
-          if (cns[i] < 0 && cns[i] <= -3) {
+          if (cns[i] <= -2) {   // constant exterior states (walls mirror the trace: same speed)
             double px = 0.0, py = 0.0;
             if (cns[i] == -7) {
               const double s = gauss_s(NQ, nu);
               const double xa = m.vxy[(2 * ((i + 1) % 3)) * nt + Kc], ya = m.vxy[(2 * ((i + 1) % 3) + 1) * nt + Kc];
               const double xb = m.vxy[(2 * ((i + 2) % 3)) * nt + Kc], yb = m.vxy[(2 * ((i + 2) % 3) + 1) * nt + Kc];
-              px = xa + (xb - xa) * s;
-              py = ya + (yb - ya) * s;
+              px = fma(xb - xa, s, xa);
+              py = fma(yb - ya, s, ya);
             }
-            Real up[4];
-            ghost_state(-cns[i], u, nxs[i], nys[i], px, py, t_out, ph, up);
+            Real up[4], ab[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) ab[c] = Real(a0[c]);
+            ghost_state(-cns[i], u, ab, nxs[i], nys[i], px, py, t_out, ph, up);
             amax = max_nn(amax, double(wave_speed(up, nxs[i], nys[i], gamma)));
           }
         }
@@ -1013,7 +1009,7 @@ __global__ void __launch_bounds__(TPB, sizeof(Real) == 4 ? STATS_MINB_F : STATS_
             const Real *__restrict__ hsi, Real *__restrict__ ej, const Scalars *sc, double c_out) {
   if (!sc->active) return;
   stats_tile<K, Real>(m, uh, part_dev, sc, blockIdx.x);
-  edge_tile<K, Real>(m, ph, vdi, hsi, ej, sc, c_out, blockIdx.x);
+  edge_tile<K, Real>(m, ph, uh.avg, vdi, hsi, ej, sc, c_out, blockIdx.x);
 }
 
 // RIOE damping, BP limiter, traces and wave speeds of the stage result

@@ -118,7 +118,7 @@ __device__ __forceinline__ void vertex_phys(const float val[4], const float gx[4
   cs = INFINITY;
   if (val[0] > 0.0f) {
     ri = 1.0f / val[0];
-    float p = gm1 * (val[3] - 0.5f * fdot2(val[1], val[1], val[2], val[2]) * ri);
+    float p = gm1 * fmaf(-0.5f * fdot2(val[1], val[1], val[2], val[2]), ri, val[3]);
     p = p > 0.0f ? p : 0.0f;
     cs = sqrtf(gamma * p * ri);
   }
@@ -180,7 +180,7 @@ __device__ __forceinline__ void rk_tile_mixed(const MeshDev &m, const Phys &ph, 
   const int64_t Kc = tile * TPB + threadIdx.x;
   double mass[4] = {0.0, 0.0, 0.0, 0.0};
   if (Kc < nt) {
-    const double dt = sc->dt, t_in = sc->t + c_in * sc->dt;
+    const double dt = sc->dt, t_in = fma(c_in, sc->dt, sc->t);
     const float alpha = float(sc->alpha), gm1 = ph.gm1_f;
     const double area = m.area[Kc];
     const float jx = m.jinv_f[Kc], jy = m.jinv_f[nt + Kc], ex = m.jinv_f[2 * nt + Kc], ey = m.jinv_f[3 * nt + Kc];
@@ -247,16 +247,11 @@ __device__ __forceinline__ void rk_tile_mixed(const MeshDev &m, const Phys &ph, 
             constexpr double sg = gauss_s(NQ, nu);
             const double xa = m.vxy[(2 * ((i + 1) % 3)) * nt + Kc], ya = m.vxy[(2 * ((i + 1) % 3) + 1) * nt + Kc];
             const double xb = m.vxy[(2 * ((i + 2) % 3)) * nt + Kc], yb = m.vxy[(2 * ((i + 2) % 3) + 1) * nt + Kc];
-            px = xa + (xb - xa) * sg;
-            py = ya + (yb - ya) * sg;
+            px = fma(xb - xa, sg, xa);
+            py = fma(yb - ya, sg, ya);
           }
-          ghost_state(-cn, um, nx, ny, px, py, t_in, ph, up);
-          if (cn == -2) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) fp[q] = fm[q];
-          } else {
-            flux_dir_nc(up, nx, ny, gm1, fp);
-          }
+          ghost_state(-cn, um, v0r, nx, ny, px, py, t_in, ph, up);
+          flux_dir_nc(up, nx, ny, gm1, fp);
         }
         // l_i w_nu / 2: the 1/2 of the LF flux rides on the weight
         constexpr float hw = float(0.5 * gauss_w(NQ, nu));
@@ -359,7 +354,7 @@ __device__ __forceinline__ void edge_jumps_mixed(int I, const MeshDev &m, const 
       double px = 0.0, py = 0.0;
       if (cn == -7) { px = m.vxy[(2 * v0) * nt + Kc]; py = m.vxy[(2 * v0 + 1) * nt + Kc]; }
       vz[0] = 1.0f;   // an admissible dummy state: only the exterior Hessian is used here
-      ghost_vertex(-cn, vz, gz, hme, nx, ny, px, py, t_out, ph, xv, xg, xh);
+      ghost_vertex(-cn, vz, gz, hme, a0f, nx, ny, px, py, t_out, ph, xv, xg, xh);
 #pragma unroll
       for (int q = 0; q < 12; ++q) jh[q] = hme[q] - xh[q];
     }
@@ -397,8 +392,8 @@ __device__ __forceinline__ void edge_jumps_mixed(int I, const MeshDev &m, const 
       double px = 0.0, py = 0.0;
       if (cn == -7) { px = m.vxy[(2 * ov) * nt + Kc]; py = m.vxy[(2 * ov + 1) * nt + Kc]; }
       float xh[12];
-      ghost_vertex(-cn, val, grd, hme, nx, ny, px, py, t_out, ph, xv, xg, xh);
-      r_oth = cn >= -2 ? r_own : wave_speed(xv, nx, ny, gamma);
+      ghost_vertex(-cn, val, grd, hme, a0f, nx, ny, px, py, t_out, ph, xv, xg, xh);
+      r_oth = cn == -1 ? r_own : wave_speed(xv, nx, ny, gamma);   // a mirror state has the same speed
     }
     beta = max_nn(beta, max_nn(r_own, r_oth));
     float jv[4], jg[4][2];
@@ -467,12 +462,15 @@ __device__ __forceinline__ void limit_mixed(const MeshDev &m, const Phys &ph, co
     if (!avg_ok) {
       cnt[1] = 1;
     } else {
-      float S[4];
+      // |Psi_l| <= 4 on K: every point's deviation is at most D in magnitude
+      float D[4], S[4];
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        S[c] = fabsf(a0f[c]);
+        float a = 0.0f;
 #pragma unroll
-        for (int l = 1; l < NB; ++l) S[c] += 4.0f * fabsf(hi[c][l]);   // |Psi_l| <= 4 on K
+        for (int l = 1; l < NB; ++l) a += fabsf(hi[c][l]);
+        D[c] = 4.0f * a;
+        S[c] = fabsf(a0f[c]) + D[c];
       }
       auto passes = [&](const float d[4]) -> bool {
         const float r = a0f[0] + d[0];
@@ -484,9 +482,27 @@ __device__ __forceinline__ void limit_mixed(const MeshDev &m, const Phys &ph, co
         const float margin = fdot2(1e-5f, fmaf(v, S[1] + S[2], fmaf(v * v, S[0], S[3])), 1e-6f, fabsf(E) + q);
         return E - 0.5f * q >= eps2 + margin;
       };
-      // the points are evaluated one at a time (few live registers); the
+      // A bound over the whole cell settles the usual (smooth) cell without
+      // visiting its points: each point's density is at least r_lo, its
+      // energy at least E_lo and its momentum norm at most M_hi.  If these
+      // pass the point test with twice the largest margin any point could
+      // need (the doubling covers the rounding of the bound), every point
+      // passes it.  Either way a cell goes to the FP64 branch only if some
+      // point might fail, and that branch leaves an admissible cell unchanged,
+      // so the bound changes no result.
+      bool ok = false;
+      const float r_lo = a0f[0] - D[0];
+      if (r_lo >= eps1 + 2e-5f * S[0]) {
+        const float M_hi = sqrtf(fdot2(a0f[1], a0f[1], a0f[2], a0f[2])) + D[1] + D[2];
+        const float E_lo = a0f[3] - D[3], E_hi = fabsf(a0f[3]) + D[3];
+        const float v_hi = M_hi / r_lo, q_hi = M_hi * v_hi;
+        const float margin = fdot2(1e-5f, fmaf(v_hi, S[1] + S[2], fmaf(v_hi * v_hi, S[0], S[3])), 1e-6f, E_hi + q_hi);
+        ok = E_lo - 0.5f * q_hi >= eps2 + 2.0f * margin;
+      }
+      // otherwise the points one at a time (few live registers); the
       // classical decomposition's extra point needs the weighted edge sum
-      bool ok = true;
+      if (!ok) {
+      ok = true;
       float zs[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
       for (int e = 0; e < 3; ++e)
@@ -517,6 +533,7 @@ __device__ __forceinline__ void limit_mixed(const MeshDev &m, const Phys &ph, co
           }
           ok = passes(d) && ok;
         }
+      }
       }
       lim64 = !ok;
     }
@@ -551,23 +568,30 @@ __device__ __forceinline__ void limit_mixed(const MeshDev &m, const Phys &ph, co
   for (int i = 0; i < 3; ++i) {
     static_for<NQ>([&](auto nc) {
       constexpr int nu = decltype(nc)::value;
-      float u[4], f[4], d[4];
+      float u[4], d[4];
       edge_dev<K, nu>(i, hi, d);
 #pragma unroll
       for (int c = 0; c < 4; ++c) u[c] = __fadd_rn(a0f[c], d[c]);
-      const float r = flux_speed(u, nxs[i], nys[i], gm1, gamma, f);
+      // |v . n| + c (+inf for rho <= 0, pressure clamped at 0)
+      float r = INFINITY;
+      if (u[0] > 0.0f) {
+        const float ri = 1.0f / u[0];
+        float p = gm1 * fmaf(-0.5f * fdot2(u[1], u[1], u[2], u[2]), ri, u[3]);
+        p = p > 0.0f ? p : 0.0f;
+        r = fmaf(fabsf(fdot2(u[1], nxs[i], u[2], nys[i])), ri, sqrtf(gamma * p * ri));
+      }
       amax32 = (r > amax32 || r != r) ? r : amax32;
-      if (cns[i] <= -3) {
+      if (cns[i] <= -2) {   // constant exterior states (walls mirror the trace: same speed)
         double qx = 0.0, qy = 0.0;
         if (cns[i] == -7) {
           constexpr double sg = gauss_s(NQ, nu);
           const double xa = m.vxy[(2 * ((i + 1) % 3)) * nt + Kc], ya = m.vxy[(2 * ((i + 1) % 3) + 1) * nt + Kc];
           const double xb = m.vxy[(2 * ((i + 2) % 3)) * nt + Kc], yb = m.vxy[(2 * ((i + 2) % 3) + 1) * nt + Kc];
-          qx = xa + (xb - xa) * sg;
-          qy = ya + (yb - ya) * sg;
+          qx = fma(xb - xa, sg, xa);
+          qy = fma(yb - ya, sg, ya);
         }
         float up[4];
-        ghost_state(-cns[i], u, nxs[i], nys[i], qx, qy, t_out, ph, up);
+        ghost_state(-cns[i], u, a0f, nxs[i], nys[i], qx, qy, t_out, ph, up);
         const float rg = wave_speed(up, nxs[i], nys[i], gamma);
         amax32 = (rg > amax32 || rg != rg) ? rg : amax32;
       }
@@ -589,7 +613,7 @@ __device__ __forceinline__ void oe_bp_tile_mixed(const MeshDev &m, const Phys &p
   if (Kc < nt) {
     // OE exterior states at the time of the stage result; the next stage's
     // alpha there too, or at the end time after the last stage of a clamped step
-    const double dt = sc->dt, t_out = sc->t + c_out * sc->dt;
+    const double dt = sc->dt, t_out = fma(c_out, sc->dt, sc->t);
     const double t_alpha = end_of_step && sc->pad ? sc->t_end : t_out;
     double a0[4];
     float a0f[4], hi[4][NB];

@@ -149,7 +149,9 @@ def _cell_expected(tag, k, t, with_ghost=True):
                 x0, ang, spd, pre, post = shock
                 xs = x0 + P[1] / math.tan(ang) + spd * t / math.sin(ang)
                 s = bc_state[post if P[0] < xs else pre]
-            else:   # a mirror or a copy of the interior has the same spectral radius
+            elif tag == 2:   # transmissive: the cell average (density at the centroid, same v and p)
+                s = _cons(rho(*V.mean(axis=0)), v0[0], v0[1], p0)
+            else:   # a mirror of the interior has the same spectral radius
                 continue
             r = s[0]
             vx, vy = s[1] / r, s[2] / r
@@ -244,8 +246,8 @@ def test_step_time_step(oracle_mod, k):
 MUTANTS = {
     "no_sound_speed": ("return fabs(u[1] * n[0] + u[2] * n[1]) / u[0] + sqrt(gamma * p / u[0]);",
                        "return fabs(u[1] * n[0] + u[2] * n[1]) / u[0];"),
-    "no_exterior": ("      if (m->nbr[3 * K + i] < 0) {\n        double uex[4];",
-                    "      if (0) {\n        double uex[4];"),
+    "no_exterior": ("      if (m->nbr[3 * K + i] < 0) {\n        double uex[4], ubar[4];",
+                    "      if (0) {\n        double uex[4], ubar[4];"),
     "cell_average": ("      eval_at(m, cf->k, u, K, &g, x, y, uin);\n      double r = wave_speed",
                      "      eval_at(m, cf->k, u, K, &g, (g.v[0][0] + g.v[1][0] + g.v[2][0]) / 3.0,\n"
                      "              (g.v[0][1] + g.v[1][1] + g.v[2][1]) / 3.0, uin);\n      double r = wave_speed"),

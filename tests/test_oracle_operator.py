@@ -57,7 +57,9 @@ def test_conservation_periodic(oracle_mod, k):
 def test_polynomial_flux_is_exact(oracle_mod, k):
     """For a global state with constant velocity v and density / pressure in
     P^k, the Euler flux is itself in P^k, traces agree across edges and the
-    quadratures are exact, so L(u) is the L2 projection of -div F(u)."""
+    quadratures are exact, so L(u) is the L2 projection of -div F(u) in every
+    cell whose edges are all interior (a transmissive edge takes the cell
+    average as exterior state, pinned separately below)."""
     O = oracle_mod
     rng = np.random.default_rng(30 + k)
     mesh = W.jittered_grid(6, 5, (-0.5, 1.0, 0.0, 1.2), seed=4,
@@ -82,7 +84,45 @@ def test_polynomial_flux_is_exact(oracle_mod, k):
     cf = O.make_config(k)
     L = om.L(cf, u, alpha=3.0)
     expect = om.project(k, fn=minus_div)
-    assert np.abs(L - expect).max() < 1e-11 * max(1.0, np.abs(expect).max())
+    nbr, _ = om.neighbors()
+    inner = (nbr >= 0).all(1)
+    assert inner.sum() >= 12
+    assert np.abs(L[:, :, inner] - expect[:, :, inner]).max() < 1e-11 * max(1.0, np.abs(expect).max())
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_transmissive_exterior_is_the_cell_average(oracle_mod, k):
+    """A single cell with transmissive edges: mode 0 of L is
+    -1/|K| sum_i l_i sum_nu w_nu Fhat(u(x_nu), ubar, n_i), with the LF flux of
+    eq. fluxLF, the exact cell average ubar as exterior state, Gauss points
+    from numpy and the Euler flux restated here."""
+    O = oracle_mod
+    rng = np.random.default_rng(70 + k)
+    V = np.array([[0.1, 0.0], [1.0, 0.2], [0.25, 0.9]])
+    tri = np.array([[0, 1, 2]], np.int32)
+    bc = np.full((1, 3), W.BC_TRANSMISSIVE, np.int8)
+    om = O.OracleMesh(V, tri, None, bc)
+    polys = [PhysPoly.random(k, rng, 0.1 * b) + PhysPoly({(0, 0): b}) for b in (1.3, 0.4, -0.3, 2.9)]
+    u = om.project(k, fn=lambda x, y: np.stack([p(x, y) for p in polys], -1))
+    from tests.helpers import tri_integral
+    area = 0.5 * ((V[1, 0] - V[0, 0]) * (V[2, 1] - V[0, 1]) - (V[2, 0] - V[0, 0]) * (V[1, 1] - V[0, 1]))
+    ubar = np.array([tri_integral(p, V) / area for p in polys])
+    alpha = 2.7
+    cf = O.make_config(k)
+    L = om.L(cf, u, alpha=alpha)
+    xg, wg = np.polynomial.legendre.leggauss(k + 1)
+    acc = np.zeros(4)
+    for i in range(3):
+        a, b = V[(i + 1) % 3], V[(i + 2) % 3]
+        d = b - a
+        ln = math.hypot(*d)
+        n = np.array([d[1], -d[0]]) / ln
+        for s, w in zip(0.5 * (1 + xg), 0.5 * wg):
+            P = a + s * d
+            um = np.array([p(*P) for p in polys])
+            fh = 0.5 * (euler_flux_n(um, n) + euler_flux_n(ubar, n) - alpha * (ubar - um))
+            acc -= ln * w * fh
+    np.testing.assert_allclose(L[:, 0, 0], acc / area, rtol=1e-11, atol=1e-13 * np.abs(acc / area).max())
 
 
 def test_piecewise_constant_reduces_to_fv_lf(oracle_mod):
