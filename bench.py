@@ -72,10 +72,6 @@ TRAFFIC_PER_LAUNCH = {"rk": 1.737e9, "stats": 0.947e9, "oe_bp": 1.376e9}
 S_MIXED_P2 = 112.0
 ALGO_BYTES_MIXED_P2 = {"rk": (8.0 / 3.0) * S_MIXED_P2 + 80.0, "stats": S_MIXED_P2,
                        "oe_bp": 2.0 * S_MIXED_P2 + 92.0}
-# bytes the kernels' own design moves besides those: the exchange buffers
-# written by one pass and read by the next (traces of the stage input 144,
-# vertex records 192, Hessians 48, per-edge OE records 1.5 x 64 per cell)
-DESIGN_BYTES_MIXED_P2 = {"rk": 800.0, "stats": 474.0, "oe_bp": 552.0}
 # DRAM bytes per launch of the mixed-form kernels from one ncu capture
 TRAFFIC_MIXED_PER_LAUNCH = {"rk": 0.713e9, "stats": 0.495e9, "oe_bp": 0.554e9}
 
@@ -407,20 +403,23 @@ def main():
                 k2 = {k: v for k, v in prof2.items() if v[1] > 0}
                 tot2 = sum(v[0] for v in k2.values())
                 mixed["kernel_share"] = {k: round(v[0] / tot2, 4) for k, v in k2.items()}
-                # HBM roofline of the dominant mixed-form kernel
-                dom2 = max(k2, key=lambda k: k2[k][0])
-                avg2 = k2[dom2][0] / k2[dom2][1]
+                # HBM roofline of each stage kernel of the mixed form on the
+                # method's bytes, the dominant one as the line's roofline
                 hbm = peaks.get("hbm_gbs", 6800.0)
-                if dom2 in ALGO_BYTES_MIXED_P2 and wl.k == 2:
-                    gbs = ALGO_BYTES_MIXED_P2[dom2] * nt / (avg2 / 1e3) / 1e9
-                    dgbs = DESIGN_BYTES_MIXED_P2[dom2] * nt / (avg2 / 1e3) / 1e9
-                    mixed["roofline"] = {"bound": "hbm", "kernel": dom2, "achieved": gbs, "peak": hbm, "unit": "GB/s",
-                                         "frac": gbs / hbm, "traffic": TRAFFIC_MIXED_PER_LAUNCH.get(dom2),
-                                         "peak_source": f"{peak_src} HBM copy bandwidth",
-                                         "algorithmic_bytes_per_cell": ALGO_BYTES_MIXED_P2[dom2],
-                                         "design_bytes_per_cell": DESIGN_BYTES_MIXED_P2[dom2],
-                                         "design_frac": dgbs / hbm,
-                                         "avg_launch_ms": avg2}
+                if wl.k == 2:
+                    per = {}
+                    for kk in ("rk", "stats", "oe_bp"):
+                        if kk not in k2:
+                            continue
+                        avg_k = k2[kk][0] / k2[kk][1]
+                        gbs = ALGO_BYTES_MIXED_P2[kk] * nt / (avg_k / 1e3) / 1e9
+                        per[kk] = {"bound": "hbm", "kernel": kk, "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                                   "frac": gbs / hbm, "traffic": TRAFFIC_MIXED_PER_LAUNCH.get(kk),
+                                   "peak_source": f"{peak_src} HBM copy bandwidth",
+                                   "algorithmic_bytes_per_cell": ALGO_BYTES_MIXED_P2[kk], "avg_launch_ms": avg_k}
+                    dom2 = max(per, key=lambda kk: per[kk]["avg_launch_ms"])
+                    mixed["roofline"] = per[dom2]
+                    mixed["kernel_rooflines"] = per
                     mixed["step_hbm_frac"] = (sum(ALGO_BYTES_MIXED_P2.values()) * nt * 3 * args.steps
                                               / (ms2 / 1e3) / 1e9 / hbm)
             del s2

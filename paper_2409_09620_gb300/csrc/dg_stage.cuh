@@ -858,7 +858,36 @@ __device__ __forceinline__ void oe_bp_tile(const MeshDev &m, const Phys &ph, Sta
           }
         }
       double th_r = 1.0, th_a = 1.0;
-      if (do_bp) {
+      // A bound over the whole cell settles the usual (smooth) cell without
+      // its limiter points: with |Psi_l| <= 4 on K, every point's density is
+      // at least rho_bar - 4 sum |rho_l|, its energy at least E_bar -
+      // 4 sum |E_l| and the L1 norm of its momentum at most |m1_bar| +
+      // |m2_bar| + 4 sum (|m1_l| + |m2_l|).  If these keep rho and the
+      // internal energy above the thresholds with a margin far above the
+      // rounding of the point evaluations, every point passes the paper's
+      // tests and theta = 1, as the points themselves would give.
+      const double Ebar = int_energy(a0);
+      bool settled = false;
+      if (do_bp && a0[0] > 0.0 && Ebar > 0.0) {
+        double D[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          double s = 0.0;
+#pragma unroll
+          for (int l = 1; l < NB; ++l) s += fabs(double(hi[c][l]));
+          D[c] = 4.0 * s;
+        }
+        const double eps1 = fmin(a0[0], 1e-13), eps2 = fmin(Ebar, 1e-13);
+        const double r_lo = a0[0] - D[0];
+        if (r_lo >= fma(1e-12, a0[0] + D[0], eps1)) {
+          const double M_hi = (fabs(a0[1]) + fabs(a0[2])) + (D[1] + D[2]);
+          const double E_lo = a0[3] - D[3], E_hi = fabs(a0[3]) + D[3];
+          // E_lo - M_hi^2 / (2 r_lo) >= eps2 + 1e-12 (E_hi + M_hi^2 / r_lo), times r_lo > 0
+          const double M2 = M_hi * M_hi;
+          settled = r_lo * (E_lo - eps2) - 1e-12 * fma(E_hi, r_lo, M2) >= 0.5 * M2;
+        }
+      }
+      if (do_bp && !settled) {
         if (ph.decomp) {
           zxs_extra_points<K, double, NE + 2>(dev);
         } else {
@@ -888,7 +917,6 @@ __device__ __forceinline__ void oe_bp_tile(const MeshDev &m, const Phys &ph, Sta
               dev[NE + p][c] = s;
             }
         }
-        const double Ebar = int_energy(a0);
         if (!(a0[0] > 0.0) || !(Ebar > 0.0)) {
           cnt[1] = 1;
         } else {
