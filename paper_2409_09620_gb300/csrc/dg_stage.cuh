@@ -584,158 +584,6 @@ __device__ __forceinline__ void edge_tile(const MeshDev &m, const Phys &ph, cons
   }
 }
 
-// The FP64 branch of limit_and_trace_mixed for cells that fail the FP32
-// screen (rare: cells where the limiter acts).  Kept out of line so that its
-// registers do not weigh on the common path.  hi, a0: the cell's modes and
-// averages; px, py: the extra limiter points; ut: traces of the stored state
-// at the edge Gauss points (out); limited: set when theta < 1 or the cell
-// fell back to its average.
-template <int K>
-__device__ __noinline__ void limit_mixed_fp64(const MeshDev &m, const Phys &ph, const double *a0p, const float *hip,
-                                              StateDev<float> out, int64_t Kc, float *utp, long long *limited) {
-  constexpr int NB = Deg<K>::NB, NQ = Deg<K>::NQ, NE = 3 * NQ;
-  const int64_t nt = m.nt;
-  double a0[4], px[2], py[2];
-  float hi[4][NB];
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    a0[c] = a0p[c];
-#pragma unroll
-    for (int l = 0; l < NB; ++l) hi[c][l] = hip[c * NB + l];
-  }
-  // the two extra points of the limiter set in FP64 (P1: vertices v1, v2; P2: internal nodes)
-  if (K == 1) {
-    const int v1 = m.limv[Kc], v2 = m.limv[nt + Kc];
-    px[0] = vert_xi(v1); py[0] = vert_eta(v1); px[1] = vert_xi(v2); py[1] = vert_eta(v2);
-  } else {
-    px[0] = m.node[Kc]; py[0] = m.node[nt + Kc]; px[1] = m.node[2 * nt + Kc]; py[1] = m.node[3 * nt + Kc];
-  }
-  float ut[NE][4];
-  long long cnt[1] = {0};
-    // ---- FP64 theta (Sec. 4.4 Steps 1-2) with targets covering the FP32 store
-    double d[NE + 2][4], Sa[4];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      Sa[c] = 0.0;
-#pragma unroll
-      for (int l = 1; l < NB; ++l) Sa[c] += fabs(double(hi[c][l]));
-    }
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int nu = 0; nu < NQ; ++nu) {
-        const double xi = edge_xi(i, gauss_s(NQ, nu)), eta = edge_eta(i, gauss_s(NQ, nu));
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          double sacc = 0.0;
-#pragma unroll
-          for (int l = 1; l < NB; ++l) sacc = cfma(psi(l, xi, eta), double(hi[c][l]), sacc);
-          d[i * NQ + nu][c] = sacc;
-        }
-      }
-    if (ph.decomp) {
-      zxs_extra_points<K, double, NE + 2>(d);
-    } else {
-#pragma unroll
-      for (int p = 0; p < 2; ++p)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          double sacc = 0.0;
-#pragma unroll
-          for (int l = 1; l < NB; ++l) sacc = fma(psi(l, px[p], py[p]), double(hi[c][l]), sacc);
-          d[NE + p][c] = sacc;
-        }
-    }
-    const double r22 = 2.384185791015625e-07;   // 2^-22: |Psi| <= 4 times the FP32 half-ulp 2^-24
-    const double Ebar = int_energy(a0);
-    double rmin = INFINITY;
-#pragma unroll
-    for (int p = 0; p < NE + 2; ++p) rmin = fmin(rmin, a0[0] + d[p][0]);
-    const double eps1 = fmin(a0[0], 1e-13);
-    const double tgt1 = fmin(a0[0], fma(2.0 * r22, Sa[0], eps1));
-    const double th1 = rmin < tgt1 ? (a0[0] - tgt1) / (a0[0] - rmin) : 1.0;
-    double emin = INFINITY, vmax2 = 0.0;
-#pragma unroll
-    for (int p = 0; p < NE + 2; ++p) {
-      const double w0 = fma(th1, d[p][0], a0[0]), w1 = a0[1] + d[p][1], w2 = a0[2] + d[p][2], w3 = a0[3] + d[p][3];
-      const double q = fdot2(w1, w1, w2, w2);
-      vmax2 = fmax(vmax2, q / (w0 * w0));
-      emin = fmin(emin, w3 - 0.5 * q / w0);
-    }
-    const double RE = r22 * fma(sqrt(vmax2), Sa[1] + Sa[2], fma(vmax2 * th1, Sa[0], Sa[3]));
-    const double eps2 = fmin(Ebar, 1e-13);
-    const double tgt2 = fmin(Ebar, fma(2.0, RE, eps2));
-    const double th2 = emin < tgt2 ? (Ebar - tgt2) / (Ebar - emin) : 1.0;
-    float hs[4][NB];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      hs[c][0] = 0.0f;
-#pragma unroll
-      for (int l = 1; l < NB; ++l) hs[c][l] = float((c == 0 ? th1 * th2 : th2) * double(hi[c][l]));
-    }
-    // verify the stored FP32 modes in FP64 at every point of the set
-    bool bad = false;
-    double ud[NE][4], vd2[NE + 2][4];
-#pragma unroll
-    for (int p = 0; p < NE; ++p) {
-      const int i = p / NQ, nu = p % NQ;
-      const double xi = edge_xi(i, gauss_s(NQ, nu)), eta = edge_eta(i, gauss_s(NQ, nu));
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        double sacc = 0.0;
-#pragma unroll
-        for (int l = 1; l < NB; ++l) sacc = cfma(psi(l, xi, eta), double(hs[c][l]), sacc);
-        vd2[p][c] = sacc;
-        ud[p][c] = a0[c] + sacc;
-      }
-    }
-    if (ph.decomp) {
-      zxs_extra_points<K, double, NE + 2>(vd2);
-    } else {
-#pragma unroll
-      for (int p = 0; p < 2; ++p)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          double sacc = 0.0;
-#pragma unroll
-          for (int l = 1; l < NB; ++l) sacc = fma(psi(l, px[p], py[p]), double(hs[c][l]), sacc);
-          vd2[NE + p][c] = sacc;
-        }
-    }
-#pragma unroll
-    for (int p = 0; p < NE + 2; ++p) {
-      double w[4];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) w[c] = a0[c] + vd2[p][c];
-      if (!(w[0] > 0.0) || !(int_energy(w) > 0.0)) bad = true;
-    }
-    if (bad) {
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-#pragma unroll
-        for (int l = 1; l < NB; ++l) hs[c][l] = 0.0f;
-#pragma unroll
-        for (int p = 0; p < NE; ++p) ud[p][c] = a0[c];
-      }
-    }
-    if (th1 < 1.0 || th2 < 1.0 || bad) cnt[0] = 1;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      out.avg[c * nt + Kc] = a0[c];
-#pragma unroll
-      for (int l = 1; l < NB; ++l) out.hi[(c * (NB - 1) + (l - 1)) * nt + Kc] = hs[c][l];
-    }
-#pragma unroll
-    for (int p = 0; p < NE; ++p)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) ut[p][c] = float(ud[p][c]);
-  #pragma unroll
-  for (int p = 0; p < NE; ++p)
-#pragma unroll
-    for (int c = 0; c < 4; ++c) utp[p * 4 + c] = ut[p][c];
-  *limited = cnt[0];
-}
-
 template <int K, typename Real>
 __device__ __forceinline__ void oe_bp_tile(const MeshDev &m, const Phys &ph, StateDev<Real> uh, StateDev<Real> out,
                                            const Real *__restrict__ ej,

@@ -180,7 +180,7 @@ __device__ __forceinline__ void rk_tile_mixed(const MeshDev &m, const Phys &ph, 
   const int64_t Kc = tile * TPB + threadIdx.x;
   double mass[4] = {0.0, 0.0, 0.0, 0.0};
   if (Kc < nt) {
-    const double dt = sc->dt, t_in = fma(c_in, sc->dt, sc->t);
+    const double dt = sc->dt;
     const float alpha = float(sc->alpha), gm1 = ph.gm1_f;
     const double area = m.area[Kc];
     const float jx = m.jinv_f[Kc], jy = m.jinv_f[nt + Kc], ex = m.jinv_f[2 * nt + Kc], ey = m.jinv_f[3 * nt + Kc];
@@ -242,13 +242,14 @@ __device__ __forceinline__ void rk_tile_mixed(const MeshDev &m, const Phys &ph, 
           for (int q = 0; q < 4; ++q) up[q] = __fadd_rn(nbr[q], d[q]);
           flux_dir_nc(up, nx, ny, gm1, fp);   // = -F(u+).n of the neighbour, n+ = -n exactly
         } else {
-          double px = 0.0, py = 0.0;
-          if (cn == -7) {
+          double px = 0.0, py = 0.0, t_in = 0.0;
+          if (cn == -7) {   // the time-dependent exterior state needs the point and the stage time
             constexpr double sg = gauss_s(NQ, nu);
             const double xa = m.vxy[(2 * ((i + 1) % 3)) * nt + Kc], ya = m.vxy[(2 * ((i + 1) % 3) + 1) * nt + Kc];
             const double xb = m.vxy[(2 * ((i + 2) % 3)) * nt + Kc], yb = m.vxy[(2 * ((i + 2) % 3) + 1) * nt + Kc];
             px = fma(xb - xa, sg, xa);
             py = fma(yb - ya, sg, ya);
+            t_in = fma(c_in, sc->dt, sc->t);
           }
           ghost_state(-cn, um, v0r, nx, ny, px, py, t_in, ph, up);
           flux_dir_nc(up, nx, ny, gm1, fp);
@@ -420,18 +421,214 @@ __device__ __forceinline__ void edge_jumps_mixed(int I, const MeshDev &m, const 
   }
 }
 
-// BP limiter of the mixed form (FP32 screen, FP64 theta where it fails) and
-// the wave speeds of the stored result at the edge Gauss points (and of the
-// exterior states of constant-state boundaries) for alpha.  The traces are
-// evaluated from the stored modes exactly as the flux pass evaluates them.
+// ---------------------------------------------------------------------------
+// FP64 theta of the mixed form (Sec. 4.4 Steps 1-2), one warp per cell
+// ---------------------------------------------------------------------------
+// The limiter point set of a P_K cell: the 3 (K + 1) edge Gauss points, then
+// two extra points (the internal nodes of the optimal decomposition for P2,
+// the vertices v1, v2 for P1; with the classical decomposition both extra
+// rows are the weighted edge combination of zxs_extra_points).  LimTab holds,
+// per point, psi_1 .. psi_{NB-1} there; the node rows come from the mesh.
 template <int K>
-__device__ __forceinline__ void limit_mixed(const MeshDev &m, const Phys &ph, const double a0[4],
-                                            float hi[4][Deg<K>::NB], const float nxs[3], const float nys[3],
-                                            const int32_t cns[3], StateDev<float> out, int64_t Kc, double t_out,
-                                            int do_bp, double &amax, long long cnt[2]) {
-  constexpr int NB = Deg<K>::NB, NQ = Deg<K>::NQ, NE = 3 * NQ;
+struct LimTab {
+  static constexpr int NQ = K + 1, NE = 3 * NQ, NP = NE + 2, NB = Deg<K>::NB;
+  double v[NP][NB];
+};
+template <int K>
+constexpr LimTab<K> make_lim_tab() {
+  LimTab<K> t{};
+  constexpr int NQ = LimTab<K>::NQ, NE = LimTab<K>::NE, NB = LimTab<K>::NB;
+  for (int p = 0; p < NE; ++p) {
+    const double sg = gauss_s(NQ, p % NQ);
+    for (int l = 0; l < NB; ++l) t.v[p][l] = psi(l, edge_xi(p / NQ, sg), edge_eta(p / NQ, sg));
+  }
+  for (int l = 0; l < NB; ++l) {
+    double acc = 0.0;   // classical extra row: P1 the first edge point, P2 -1/6 sum_p w_p psi(x_p)
+    for (int p = 0; p < NE; ++p) acc += gauss_w(NQ, p % NQ) * t.v[p][l];
+    const double v = K == 1 ? t.v[0][l] : (-1.0 / 6.0) * acc;
+    t.v[NE][l] = v;
+    t.v[NE + 1][l] = v;
+  }
+  return t;
+}
+static __device__ const LimTab<1> g_lim_tab1 = make_lim_tab<1>();
+static __device__ const LimTab<2> g_lim_tab2 = make_lim_tab<2>();
+
+// per-warp scratch of the cooperative limiter: the cell's averages, modes in
+// FP64, the scaled modes (FP32 and back in FP64) and the scalars of its theta
+template <int K>
+struct LimScratch {
+  static constexpr int NM = 4 * (Deg<K>::NB - 1);
+  double a0[4], hd[NM], hsd[NM], sa[4];
+  float hs[NM];
+};
+
+// Warp reductions over the limiter points (lanes beyond the set hold the
+// identity): minimum on the integer units through order-preserving keys,
+// maximum of non-negative values on their bit patterns.
+__device__ __forceinline__ double warp_min_ord(double x) {
+  long long k = ord_key(x);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) k = min(k, __shfl_xor_sync(0xffffffffu, k, o));
+  return ord_val(k);
+}
+__device__ __forceinline__ double warp_max_nn(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x = max_nn(x, __shfl_xor_sync(0xffffffffu, x, o));
+  return x;
+}
+
+// FP64 theta for the cells of this warp that failed the FP32 screen (flag).
+// The warp takes them one at a time; lane p evaluates limiter point p and
+// lane j scales mode j, so the serial FP64 work of a cell (well over a
+// thousand FP64 instructions, which GB300's narrow FP64 pipe runs at about
+// one warp instruction per 64 cycles per scheduler) shrinks to about a
+// hundred and fifty warp instructions.  The targets cover the rounding of
+// the FP32 store (2^-22 per unit of sum |mode|, |Psi| <= 4 on K); the stored
+// FP32 modes are then verified in FP64 at every point of the set, and a cell
+// that still fails keeps its average only.  On return a flagged lane's hi
+// holds the stored modes; limited is set when theta < 1 or the cell fell back
+// to its average.  Every lane of the warp calls this (the shuffles and
+// warp barriers take all 32).
+template <int K>
+__device__ __forceinline__ void limit_fp64_warp(const MeshDev &m, const Phys &ph, bool flag, int64_t Kc,
+                                                const double a0[4], float hi[4][Deg<K>::NB], StateDev<float> out,
+                                                long long &limited) {
+  constexpr int NB = Deg<K>::NB, NQ = K + 1, NE = 3 * NQ, NP = NE + 2, NM = 4 * (NB - 1);
+  static_assert(NP <= 32 && NM <= 32, "one lane per point and per mode");
+  const unsigned FULL = 0xffffffffu;
+  unsigned todo = __ballot_sync(FULL, flag);
+  if (todo == 0u) return;
+  __shared__ LimScratch<K> scr_all[TPB / 32];
+  LimScratch<K> &S = scr_all[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
   const int64_t nt = m.nt;
-  const float gamma = ph.gamma_f, gm1 = ph.gm1_f;
+  const double r22 = 2.384185791015625e-07;   // 2^-22
+  // this lane's basis values at its point (edge rows; extra rows per cell below)
+  double psv[NB];
+  const bool on_pt = lane < NP;
+  const int prow = on_pt ? lane : 0;
+#pragma unroll
+  for (int l = 1; l < NB; ++l) psv[l] = K == 1 ? g_lim_tab1.v[prow][l] : g_lim_tab2.v[prow][l];
+  const bool node_row = on_pt && lane >= NE && !ph.decomp;
+  while (todo) {
+    const int src = __ffs(todo) - 1;
+    todo &= todo - 1u;
+    const int64_t Ks = __shfl_sync(FULL, Kc, src);
+    if (lane == src) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) S.a0[c] = a0[c];
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int l = 1; l < NB; ++l) S.hs[c * (NB - 1) + l - 1] = hi[c][l];
+    }
+    __syncwarp();
+    if (lane < NM) S.hd[lane] = double(S.hs[lane]);
+    if (node_row) {   // the extra point of this cell: P2 internal node, P1 vertex
+      const int e = lane - NE;
+      if (K == 1) {
+        const int vp = m.limv[e * nt + Ks];
+#pragma unroll
+        for (int l = 1; l < NB; ++l) psv[l] = psi(l, vert_xi(vp), vert_eta(vp));
+      } else {
+#pragma unroll
+        for (int l = 1; l < NB; ++l) psv[l] = m.psi_node[(5 * e + l - 1) * nt + Ks];
+      }
+    }
+    __syncwarp();
+    if (lane < 4) {
+      double sa = 0.0;
+#pragma unroll
+      for (int l = 1; l < NB; ++l) sa += fabs(S.hd[lane * (NB - 1) + l - 1]);
+      S.sa[lane] = sa;
+    }
+    double A[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) A[c] = S.a0[c];
+    // deviations of the unlimited polynomial at this lane's point
+    double d[4] = {0.0, 0.0, 0.0, 0.0};
+    if (on_pt) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        double acc = 0.0;
+#pragma unroll
+        for (int l = 1; l < NB; ++l) acc = fma(psv[l], S.hd[c * (NB - 1) + l - 1], acc);
+        d[c] = acc;
+      }
+    }
+    __syncwarp();
+    double Sa[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) Sa[c] = S.sa[c];
+    // Step 1: density
+    const double rmin = warp_min_ord(on_pt ? A[0] + d[0] : INFINITY);
+    const double eps1 = fmin(A[0], 1e-13);
+    const double tgt1 = fmin(A[0], fma(2.0 * r22, Sa[0], eps1));
+    const double th1 = rmin < tgt1 ? (A[0] - tgt1) / (A[0] - rmin) : 1.0;
+    // Step 2: internal energy of the density-limited polynomial; the target
+    // covers the FP32 store through the largest squared speed on the set
+    const double w0 = fma(th1, d[0], A[0]), w1 = A[1] + d[1], w2 = A[2] + d[2], w3 = A[3] + d[3];
+    const double q = fdot2(w1, w1, w2, w2);
+    const double v2 = q / (w0 * w0);
+    const double vmax2 = warp_max_nn(on_pt && v2 == v2 ? v2 : 0.0);   // a NaN is ignored, as by fmax
+    const double Ebar = int_energy(A);
+    const double RE = r22 * fma(sqrt(vmax2), Sa[1] + Sa[2], fma(vmax2 * th1, Sa[0], Sa[3]));
+    const double eps2 = fmin(Ebar, 1e-13);
+    const double tgt2 = fmin(Ebar, fma(2.0, RE, eps2));
+    // E - |m|^2 / (2 rho) < tgt2 tested as rho E - |m|^2 / 2 < tgt2 rho (rho > 0):
+    // the division only at points that violate the target
+    double e_pt = INFINITY;
+    if (on_pt && (!(w0 > 0.0) || fma(w3, w0, -0.5 * q) < tgt2 * w0)) e_pt = w3 - 0.5 * q / w0;
+    const double emin = warp_min_ord(e_pt);
+    const double th2 = emin < tgt2 ? (Ebar - tgt2) / (Ebar - emin) : 1.0;
+    // the scaled modes, one per lane, stored in FP32 and read back in FP64
+    if (lane < NM) {
+      const double th = lane < NB - 1 ? th1 * th2 : th2;
+      const float h = float(th * S.hd[lane]);
+      S.hs[lane] = h;
+      S.hsd[lane] = double(h);
+    }
+    __syncwarp();
+    // verify the stored modes at every point of the set
+    bool bad_pt = false;
+    if (on_pt) {
+      double v[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        double acc = 0.0;
+#pragma unroll
+        for (int l = 1; l < NB; ++l) acc = fma(psv[l], S.hsd[c * (NB - 1) + l - 1], acc);
+        v[c] = A[c] + acc;
+      }
+      bad_pt = !(v[0] > 0.0) || !(fma(v[3], v[0], -0.5 * fdot2(v[1], v[1], v[2], v[2])) > 0.0);
+    }
+    const bool bad = __any_sync(FULL, bad_pt);
+    if (lane == src) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int l = 1; l < NB; ++l) {
+          const float h = bad ? 0.0f : S.hs[c * (NB - 1) + l - 1];
+          hi[c][l] = h;
+          out.hi[(c * (NB - 1) + (l - 1)) * nt + Kc] = h;
+        }
+      if (th1 < 1.0 || th2 < 1.0 || bad) limited = 1;
+    }
+    __syncwarp();
+  }
+}
+
+// FP32 screen of the BP limiter (Sec. 4.4) in the mixed form.  Stores the
+// averages, and the modes of every cell that passes; returns true for a cell
+// whose theta must be taken in FP64 (limit_fp64_warp).  cnt[1] counts a cell
+// average outside G (left unlimited).
+template <int K>
+__device__ __forceinline__ bool limit_screen_mixed(const MeshDev &m, const Phys &ph, const double a0[4],
+                                                   const float a0f[4], const float hi[4][Deg<K>::NB],
+                                                   StateDev<float> out, int64_t Kc, int do_bp, long long cnt[2]) {
+  constexpr int NB = Deg<K>::NB, NQ = Deg<K>::NQ;
+  const int64_t nt = m.nt;
   float px[2], py[2];
   if (K == 1) {
     const int v1 = m.limv[Kc], v2 = m.limv[nt + Kc];
@@ -441,8 +638,6 @@ __device__ __forceinline__ void limit_mixed(const MeshDev &m, const Phys &ph, co
   }
 #pragma unroll
   for (int c = 0; c < 4; ++c) out.avg[c * nt + Kc] = a0[c];
-  float a0f[4];
-  to_real(a0, a0f);
   bool avg_ok;
   float eps1, eps2;
   {
@@ -487,9 +682,9 @@ __device__ __forceinline__ void limit_mixed(const MeshDev &m, const Phys &ph, co
       // energy at least E_lo and its momentum norm at most M_hi.  If these
       // pass the point test with twice the largest margin any point could
       // need (the doubling covers the rounding of the bound), every point
-      // passes it.  Either way a cell goes to the FP64 branch only if some
-      // point might fail, and that branch leaves an admissible cell unchanged,
-      // so the bound changes no result.
+      // passes it.  Either way a cell goes to the FP64 theta only if some
+      // point might fail, and that leaves an admissible cell unchanged, so
+      // the bound changes no result.
       bool ok = false;
       const float r_lo = a0f[0] - D[0];
       if (r_lo >= eps1 + 2e-5f * S[0]) {
@@ -502,38 +697,38 @@ __device__ __forceinline__ void limit_mixed(const MeshDev &m, const Phys &ph, co
       // otherwise the points one at a time (few live registers); the
       // classical decomposition's extra point needs the weighted edge sum
       if (!ok) {
-      ok = true;
-      float zs[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        ok = true;
+        float zs[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
-      for (int e = 0; e < 3; ++e)
-        static_for<NQ>([&](auto nc) {
-          constexpr int nu = decltype(nc)::value;
+        for (int e = 0; e < 3; ++e)
+          static_for<NQ>([&](auto nc) {
+            constexpr int nu = decltype(nc)::value;
+            float d[4];
+            edge_dev<K, nu>(e, hi, d);
+            ok = passes(d) && ok;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) zs[c] += float(gauss_w(NQ, nu)) * d[c];
+          });
+        if (ph.decomp) {
           float d[4];
-          edge_dev<K, nu>(e, hi, d);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) d[c] = K == 1 ? 0.0f : float(-1.0 / 6.0) * zs[c];
+          if (K == 1) edge_dev<K, 0>(0, hi, d);   // P1: the edge weights sum to one (see zxs_extra_points)
           ok = passes(d) && ok;
+        } else {
 #pragma unroll
-          for (int c = 0; c < 4; ++c) zs[c] += float(gauss_w(NQ, nu)) * d[c];
-        });
-      if (ph.decomp) {
-        float d[4];
+          for (int p = 0; p < 2; ++p) {
+            float d[4];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) d[c] = K == 1 ? 0.0f : float(-1.0 / 6.0) * zs[c];
-        if (K == 1) edge_dev<K, 0>(0, hi, d);   // P1: the edge weights sum to one (see zxs_extra_points)
-        ok = passes(d) && ok;
-      } else {
+            for (int c = 0; c < 4; ++c) {
+              float sacc = 0.0f;
 #pragma unroll
-        for (int p = 0; p < 2; ++p) {
-          float d[4];
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            float sacc = 0.0f;
-#pragma unroll
-            for (int l = 1; l < NB; ++l) sacc = fmaf(psi_t<float>(l, px[p], py[p]), hi[c][l], sacc);
-            d[c] = sacc;
+              for (int l = 1; l < NB; ++l) sacc = fmaf(psi_t<float>(l, px[p], py[p]), hi[c][l], sacc);
+              d[c] = sacc;
+            }
+            ok = passes(d) && ok;
           }
-          ok = passes(d) && ok;
         }
-      }
       }
       lim64 = !ok;
     }
@@ -543,26 +738,20 @@ __device__ __forceinline__ void limit_mixed(const MeshDev &m, const Phys &ph, co
     for (int c = 0; c < 4; ++c)
 #pragma unroll
       for (int l = 1; l < NB; ++l) out.hi[(c * (NB - 1) + (l - 1)) * nt + Kc] = hi[c][l];
-  } else {
-    // FP64 theta (Sec. 4.4 Steps 1-2) out of line; the stored modes come back
-    double a0l[4];
-    float hl[4][NB], utl[NE][4];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      a0l[c] = reload_avg(out.avg + c * nt + Kc);
-#pragma unroll
-      for (int l = 0; l < NB; ++l) hl[c][l] = hi[c][l];
-    }
-    long long lim = 0;
-    limit_mixed_fp64<K>(m, ph, a0l, &hl[0][0], out, Kc, &utl[0][0], &lim);
-    if (lim) cnt[0] = 1;
-#pragma unroll
-    for (int c = 0; c < 4; ++c)
-#pragma unroll
-      for (int l = 1; l < NB; ++l) hi[c][l] = __ldcg(out.hi + (c * (NB - 1) + (l - 1)) * nt + Kc);
   }
-  // wave speeds at the edge Gauss points of the stored state, evaluated as
-  // the next flux pass evaluates its traces
+  return lim64;
+}
+
+// wave speeds at the edge Gauss points of the stored state (and of the
+// exterior states of constant-state boundaries), evaluated as the next flux
+// pass evaluates its traces, into amax
+template <int K>
+__device__ __forceinline__ void alpha_mixed(const MeshDev &m, const Phys &ph, const float a0f[4],
+                                            const float hi[4][Deg<K>::NB], const float nxs[3], const float nys[3],
+                                            const int32_t cns[3], int64_t Kc, double t_out, double &amax) {
+  constexpr int NQ = Deg<K>::NQ;
+  const int64_t nt = m.nt;
+  const float gamma = ph.gamma_f, gm1 = ph.gm1_f;
   float amax32 = 0.0f;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
@@ -608,18 +797,20 @@ __device__ __forceinline__ void oe_bp_tile_mixed(const MeshDev &m, const Phys &p
   constexpr int NB = Deg<K>::NB;
   const int64_t nt = m.nt;
   const int64_t Kc = tile * TPB + threadIdx.x;
+  const bool live = Kc < nt;
   double amax = 0.0;
   long long cnt[2] = {0, 0};
-  if (Kc < nt) {
-    // OE exterior states at the time of the stage result; the next stage's
-    // alpha there too, or at the end time after the last stage of a clamped step
-    const double dt = sc->dt, t_out = fma(c_out, sc->dt, sc->t);
-    const double t_alpha = end_of_step && sc->pad ? sc->t_end : t_out;
-    double a0[4];
-    float a0f[4], hi[4][NB];
+  // OE exterior states at the time of the stage result; the next stage's
+  // alpha there too, or at the end time after the last stage of a clamped step
+  const double dt = sc->dt, t_out = fma(c_out, sc->dt, sc->t);
+  const double t_alpha = end_of_step && sc->pad ? sc->t_end : t_out;
+  double a0[4] = {0.0, 0.0, 0.0, 0.0};
+  float a0f[4] = {0.0f, 0.0f, 0.0f, 0.0f}, hi[4][NB];
+  float nxs[3], nys[3];
+  int32_t cns[3];
+  bool lim64 = false;
+  if (live) {
     load_mixed<K>(uh, nt, Kc, a0, a0f, hi);
-    float nxs[3], nys[3];
-    int32_t cns[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       nxs[i] = m.nrm_f[(2 * i) * nt + Kc];
@@ -629,6 +820,7 @@ __device__ __forceinline__ void oe_bp_tile_mixed(const MeshDev &m, const Phys &p
     if (do_oe) {
       const int cw = ph.oe == 2;
       const float jx = m.jinv_f[Kc], jy = m.jinv_f[nt + Kc], ex = m.jinv_f[2 * nt + Kc], ey = m.jinv_f[3 * nt + Kc];
+      const float dtf = float(dt);
       float iD[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) iD[q] = sc->invDf[q];
@@ -696,7 +888,7 @@ __device__ __forceinline__ void oe_bp_tile_mixed(const MeshDev &m, const Phys &p
 #pragma unroll
         for (int md = 1; md <= K; ++md) {
           sacc += sig[c][md];
-          fac[c][md] = exp_neg(float(dt) * sacc);
+          fac[c][md] = exp_neg(dtf * sacc);
         }
       }
 #pragma unroll
@@ -704,8 +896,11 @@ __device__ __forceinline__ void oe_bp_tile_mixed(const MeshDev &m, const Phys &p
 #pragma unroll
         for (int l = 1; l < NB; ++l) hi[c][l] *= fac[c][degree_of(l)];
     }
-    limit_mixed<K>(m, ph, a0, hi, nxs, nys, cns, out, Kc, t_alpha, do_bp, amax, cnt);
+    lim64 = limit_screen_mixed<K>(m, ph, a0, a0f, hi, out, Kc, do_bp, cnt);
   }
+  // the FP64 theta of the cells that failed the screen, by the whole warp
+  limit_fp64_warp<K>(m, ph, lim64, Kc, a0, hi, out, cnt[0]);
+  if (live) alpha_mixed<K>(m, ph, a0f, hi, nxs, nys, cns, Kc, t_alpha, amax);
   double av[1] = {amax};
   block_reduce<1>(av, part_alpha + tile, OpMaxNN());
   __syncthreads();

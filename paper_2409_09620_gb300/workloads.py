@@ -473,9 +473,7 @@ def dmr_workload(nx=1440, ny=360, k=2, seed=3, t_end=0.2, right=BC_DIRICHLET0 + 
     """60-degree double Mach reflection on [0, 4] x [0, 1].  The right side
     holds the pre-shock state (tag 4), which is the exact solution there until
     the incident shock reaches x = 4 at t ~ 0.28; right=BC_TRANSMISSIVE gives
-    the zero-gradient outflow instead, under which the gas at rest along that
-    side develops a slowly growing boundary disturbance from round-off (seen
-    in the FP32 form on 1440 x 360 after t ~ 0.032)."""
+    the zero-gradient outflow instead (the cell average as exterior state)."""
     post, pre = dmr_states()
     x0 = 1.0 / 6.0
     bottom = lambda x, y: BC_DIRICHLET0 if x < x0 else BC_REFLECT
