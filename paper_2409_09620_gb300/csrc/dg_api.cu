@@ -315,7 +315,7 @@ int32_t upload_state(dg_solver *s, const double *coeffs, const StateBuf &b) {
     for (int c = 0; c < 4; ++c)
       for (int l = 1; l < nb; ++l)
         for (int64_t K = 0; K < nt; ++K)
-          tmp[((size_t)c * (nb - 1) + (l - 1)) * nt + K] = (float)coeffs[((int64_t)c * nb + l) * nt + K];
+          tmp[(size_t)K * 4 * (nb - 1) + c * (nb - 1) + (l - 1)] = (float)coeffs[((int64_t)c * nb + l) * nt + K];
     CUDA_TRY(cudaMemcpyAsync(b.hi, tmp.data(), sizeof(float) * tmp.size(), cudaMemcpyHostToDevice, s->stream));
     CUDA_TRY(cudaStreamSynchronize(s->stream));
   } else {
@@ -339,7 +339,7 @@ int32_t download_state(const dg_solver *s, const StateBuf &b, double *coeffs) {
     for (int c = 0; c < 4; ++c)
       for (int l = 1; l < nb; ++l)
         for (int64_t K = 0; K < nt; ++K)
-          coeffs[((int64_t)c * nb + l) * nt + K] = tmp[((size_t)c * (nb - 1) + (l - 1)) * nt + K];
+          coeffs[((int64_t)c * nb + l) * nt + K] = tmp[(size_t)K * 4 * (nb - 1) + c * (nb - 1) + (l - 1)];
   } else {
     for (int c = 0; c < 4; ++c)
       CUDA_TRY(cudaMemcpyAsync(coeffs + ((int64_t)c * nb + 1) * nt, (double *)b.hi + (int64_t)c * (nb - 1) * nt,

@@ -117,7 +117,7 @@ __device__ __forceinline__ void vstore(T *__restrict__ p, const T in[N]) {
 
 template <typename Real> struct StateDev {
   double *avg;   // [4][nt]
-  Real *hi;      // [4][nb-1][nt]
+  Real *hi;      // FP64 form: [4][nb-1][nt]; mixed form: [nt][4][nb-1] (one 16-byte aligned record per cell)
 };
 
 struct Phys {

@@ -39,15 +39,51 @@ namespace dg {
 #define OEBP_MINB_D 3
 #endif
 
+// A cell's state.  The FP64 form keeps the modes component- and mode-major
+// ([4][NB-1][nt]); the mixed form keeps each cell's 4 (NB - 1) FP32 modes
+// together (80 bytes for P2, 32 for P1, both multiples of 16), so that a cell
+// -- its own or a neighbour's -- comes in (NB - 1) 16-byte loads from one
+// address instead of 4 (NB - 1) scattered ones.
 template <typename Real, int NB>
 __device__ __forceinline__ void load_state(const StateDev<Real> &s, int64_t nt, int64_t K, double avg[4],
                                            Real hi[4][NB]) {
 #pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    avg[c] = s.avg[c * nt + K];
-    hi[c][0] = Real(0);
+  for (int c = 0; c < 4; ++c) avg[c] = s.avg[c * nt + K];
+  if constexpr (sizeof(Real) == sizeof(float)) {
+    constexpr int NM = 4 * (NB - 1);
+    const float4 *p = reinterpret_cast<const float4 *>(s.hi + K * NM);
+    float v[NM];
 #pragma unroll
-    for (int l = 1; l < NB; ++l) hi[c][l] = s.hi[(c * (NB - 1) + (l - 1)) * nt + K];
+    for (int j = 0; j < NM / 4; ++j) {
+      const float4 q = p[j];
+      v[4 * j] = q.x; v[4 * j + 1] = q.y; v[4 * j + 2] = q.z; v[4 * j + 3] = q.w;
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      hi[c][0] = Real(0);
+#pragma unroll
+      for (int l = 1; l < NB; ++l) hi[c][l] = v[c * (NB - 1) + l - 1];
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      hi[c][0] = Real(0);
+#pragma unroll
+      for (int l = 1; l < NB; ++l) hi[c][l] = s.hi[(c * (NB - 1) + (l - 1)) * nt + K];
+    }
+  }
+}
+// store the modes of cell K in the mixed form's per-cell record
+template <int NB>
+__device__ __forceinline__ void store_modes_mixed(const StateDev<float> &s, int64_t K, const float hi[4][NB]) {
+  constexpr int NM = 4 * (NB - 1);
+  float4 *p = reinterpret_cast<float4 *>(s.hi + K * NM);
+#pragma unroll
+  for (int j = 0; j < NM / 4; ++j) {
+    float q[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) q[r] = hi[(4 * j + r) / (NB - 1)][(4 * j + r) % (NB - 1) + 1];
+    p[j] = make_float4(q[0], q[1], q[2], q[3]);
   }
 }
 

@@ -299,10 +299,10 @@ __device__ __forceinline__ void rk_tile_mixed(const MeshDev &m, const Phys &ph, 
 #pragma unroll
       for (int l = 1; l < NB; ++l) {
         const float s = dtar * float(inv_mass_c(l));
-        const float hl = first ? fma(s, acc[c][l], cv[c][l]) : fdot2(ar, cu[c][l], br, fma(s, acc[c][l], cv[c][l]));
-        uh.hi[(c * (NB - 1) + (l - 1)) * nt + Kc] = hl;
+        cv[c][l] = first ? fma(s, acc[c][l], cv[c][l]) : fdot2(ar, cu[c][l], br, fma(s, acc[c][l], cv[c][l]));
       }
     }
+    store_modes_mixed<NB>(uh, Kc, cv);
   }
   block_reduce<4>(mass, part_sum + 4 * tile, OpSum());
 }
@@ -608,11 +608,8 @@ __device__ __forceinline__ void limit_fp64_warp(const MeshDev &m, const Phys &ph
 #pragma unroll
       for (int c = 0; c < 4; ++c)
 #pragma unroll
-        for (int l = 1; l < NB; ++l) {
-          const float h = bad ? 0.0f : S.hs[c * (NB - 1) + l - 1];
-          hi[c][l] = h;
-          out.hi[(c * (NB - 1) + (l - 1)) * nt + Kc] = h;
-        }
+        for (int l = 1; l < NB; ++l) hi[c][l] = bad ? 0.0f : S.hs[c * (NB - 1) + l - 1];
+      store_modes_mixed<NB>(out, Kc, hi);
       if (th1 < 1.0 || th2 < 1.0 || bad) limited = 1;
     }
     __syncwarp();
@@ -733,12 +730,7 @@ __device__ __forceinline__ bool limit_screen_mixed(const MeshDev &m, const Phys 
       lim64 = !ok;
     }
   }
-  if (!lim64) {
-#pragma unroll
-    for (int c = 0; c < 4; ++c)
-#pragma unroll
-      for (int l = 1; l < NB; ++l) out.hi[(c * (NB - 1) + (l - 1)) * nt + Kc] = hi[c][l];
-  }
+  if (!lim64) store_modes_mixed<NB>(out, Kc, hi);
   return lim64;
 }
 
