@@ -311,15 +311,18 @@ __device__ __forceinline__ void rk_tile_mixed(const MeshDev &m, const Phys &ph, 
 // K3 (mixed): RIOE from the cells' own and neighbouring polynomials, BP
 // limiter, wave speeds of the stored result at the edge Gauss points
 // ==========================================================================
+// values per vertex kept by oe_bp_tile_mixed for edge_jumps_mixed: value 4,
+// physical gradient 8, 1/rho, sound speed
+constexpr int VTX_REC = 14;
+
 // beta and the jump sums sqrt(2 J) of edge i (eqs. OEScalar:Coef2 with the
 // trapezoidal rule, RIOESys:Coef1/Coef2) seen from this cell: vertex values
 // and gradients at both endpoints, the (constant) Hessian jump once
 template <int K>
 __device__ __forceinline__ void edge_jumps_mixed(int I, const MeshDev &m, const Phys &ph, const StateDev<float> &uh,
-                                                 int64_t Kc, const float a0f[4], const float hi[4][Deg<K>::NB],
-                                                 float jx, float jy, float ex, float ey, const float hme[12],
-                                                 int32_t cn, float nx, float ny, double t_out, int cw, float &beta,
-                                                 float Jq[4][K + 1]) {
+                                                 int64_t Kc, const float a0f[4], const float (*sv)[TPB],
+                                                 const float hme[12], int32_t cn, float nx, float ny, double t_out,
+                                                 int cw, float &beta, float Jq[4][K + 1]) {
   constexpr int NB = Deg<K>::NB;
   const int64_t nt = m.nt;
   const float gamma = ph.gamma_f, gm1 = ph.gm1_f;
@@ -378,9 +381,13 @@ __device__ __forceinline__ void edge_jumps_mixed(int I, const MeshDev &m, const 
 #pragma unroll
   for (int ev = 0; ev < 2; ++ev) {
     const int ov = ev == 0 ? v0 : v1;
-    float val[4], gx[4], ge[4], grd[8], ri, cs;
-    vertex_eval<K>(ov, a0f, hi, val, gx, ge);
-    vertex_phys<K>(val, gx, ge, jx, jy, ex, ey, gamma, gm1, grd, ri, cs);
+    // this cell's value, physical gradient, 1/rho and sound speed at the vertex
+    float val[4], grd[8];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) val[q] = sv[VTX_REC * ov + q][threadIdx.x];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) grd[q] = sv[VTX_REC * ov + 4 + q][threadIdx.x];
+    const float ri = sv[VTX_REC * ov + 12][threadIdx.x], cs = sv[VTX_REC * ov + 13][threadIdx.x];
     const float r_own = fma(fabsf(fdot2(val[1], nx, val[2], ny)), ri, cs);
     float xv[4], xg[8], r_oth;
     if (cn >= 0) {
@@ -820,6 +827,25 @@ __device__ __forceinline__ void oe_bp_tile_mixed(const MeshDev &m, const Phys &p
 #pragma unroll
       for (int q = 0; q < 12; ++q) hme[q] = 0.0f;
       if constexpr (K == 2) hessian_p2(hi, jx, jy, ex, ey, hme);
+      // the cell's own vertex data, formed once (each vertex serves two
+      // edges) at compile-time vertex indices, in this thread's column of a
+      // block-shared array (no exchange between threads, so no barrier)
+      __shared__ float s_vtx[3 * VTX_REC][TPB];
+      {
+        const float gamma = ph.gamma_f, gm1 = ph.gm1_f;
+        static_for<3>([&](auto vc) {
+          constexpr int v = decltype(vc)::value;
+          float val[4], gx[4], ge[4], grd[8], ri, cs;
+          vertex_eval<K>(v, a0f, hi, val, gx, ge);
+          vertex_phys<K>(val, gx, ge, jx, jy, ex, ey, gamma, gm1, grd, ri, cs);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) s_vtx[VTX_REC * v + q][threadIdx.x] = val[q];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) s_vtx[VTX_REC * v + 4 + q][threadIdx.x] = grd[q];
+          s_vtx[VTX_REC * v + 12][threadIdx.x] = ri;
+          s_vtx[VTX_REC * v + 13][threadIdx.x] = cs;
+        });
+      }
       // sigma_q^j = sum_i (beta_i / h_i) A^{k,j} h_i^j sqrt(J) / D_q (see oe_bp_tile)
       float sig[4][K + 1];
 #pragma unroll
@@ -832,8 +858,8 @@ __device__ __forceinline__ void oe_bp_tile_mixed(const MeshDev &m, const Phys &p
 #pragma unroll 1
       for (int i = 0; i < 3; ++i) {
         float beta, Jq[4][K + 1];
-        edge_jumps_mixed<K>(i, m, ph, uh, Kc, a0f, hi, jx, jy, ex, ey, hme, m.conn[i * nt + Kc],
-                            m.nrm_f[(2 * i) * nt + Kc], m.nrm_f[(2 * i + 1) * nt + Kc], t_out, cw, beta, Jq);
+        edge_jumps_mixed<K>(i, m, ph, uh, Kc, a0f, s_vtx, hme, m.conn[i * nt + Kc], m.nrm_f[(2 * i) * nt + Kc],
+                            m.nrm_f[(2 * i + 1) * nt + Kc], t_out, cw, beta, Jq);
         float er[4][K + 1];
 #pragma unroll
         for (int j = 0; j <= K; ++j) {
