@@ -48,16 +48,17 @@ UNIT = "cell-stage updates/s"
 # deviations at the volume points 231, edge OE records 187 per edge x 1.5.
 # k_oe_bp: sigma 87, damping 38, limiter at the 11 points 497, traces and
 # wave speeds 313 (the nine reciprocal densities from one division and 24
-# multiplies).
+# multiplies); a cell that the bound over the whole cell settles skips the
+# 11 points (about 30 flops instead of 497).
 ALGO_FLOPS_P2 = {"rk": 1745.0, "stats": 512.0, "oe_bp": 935.0}
 # FP64 flops per cell-stage the hardware executed for the same kernels
 # (2 DFMA + DMUL + DADD from ncu captures / cells; k_rk: mean of its three
-# stages 1893 / 1965 / 1965); division, square root and exp expand into
+# stages 1896 / 1968 / 1968); division, square root and exp expand into
 # DFMA sequences.  None = not re-measured since the kernel last changed.
-EXECUTED_FLOPS_P2 = {"rk": 1941.0, "stats": 739.0, "oe_bp": 1175.0}
+EXECUTED_FLOPS_P2 = {"rk": 1944.0, "stats": 744.0, "oe_bp": 967.0}
 # DRAM bytes (read + write) per launch from the same captures (k_rk: mean of
-# its stages 1.596 / 1.807 / 1.807 GB).
-TRAFFIC_PER_LAUNCH = {"rk": 1.737e9, "stats": 0.947e9, "oe_bp": 1.376e9}
+# its stages 1.599 / 1.808 / 1.808 GB).
+TRAFFIC_PER_LAUNCH = {"rk": 1.738e9, "stats": 0.948e9, "oe_bp": 1.301e9}
 # Mixed form (P2, FP32 modes 1-5 and FP64 averages: S = 4 x 8 + 4 x 5 x 4 =
 # 112 B of state per cell).  Algorithmic HBM bytes per cell-stage of the
 # method's three passes, each array element moved once and neighbour data
@@ -72,8 +73,9 @@ TRAFFIC_PER_LAUNCH = {"rk": 1.737e9, "stats": 0.947e9, "oe_bp": 1.376e9}
 S_MIXED_P2 = 112.0
 ALGO_BYTES_MIXED_P2 = {"rk": (8.0 / 3.0) * S_MIXED_P2 + 80.0, "stats": S_MIXED_P2,
                        "oe_bp": 2.0 * S_MIXED_P2 + 92.0}
-# DRAM bytes per launch of the mixed-form kernels from one ncu capture
-TRAFFIC_MIXED_PER_LAUNCH = {"rk": 0.713e9, "stats": 0.495e9, "oe_bp": 0.554e9}
+# DRAM bytes per launch of the mixed-form kernels from one ncu capture (k_rk:
+# mean of its stages 272 / 394 / 394 B per cell)
+TRAFFIC_MIXED_PER_LAUNCH = {"rk": 0.366e9, "stats": 0.120e9, "oe_bp": 0.304e9}
 
 
 def load_peaks():
