@@ -100,10 +100,9 @@ __device__ __forceinline__ void eval_fixed(const A avg[4], const Real hi[4][NB],
   }
 }
 
-// In the FP32 form the FP64 averages are converted once and then let go, so
-// that the compiler cannot re-convert them at every use (each conversion is
-// an FP64-pipe instruction); the FP64 value is reloaded where it is needed
-// again.  In the FP64 form these are plain copies.
+// The averages in the working precision (plain copies in the FP64 form; the
+// mixed form's passes in dg_stage_mixed.cuh convert their own), and an FP64
+// average reloaded from memory where a converted copy was let go.
 template <typename Real>
 __device__ __forceinline__ void to_real(const double a[4], Real r[4]) {
 #pragma unroll
