@@ -216,13 +216,16 @@ int32_t dg_op_alpha(dg_solver *solver, const double *u, double t, double *alpha)
 /* Create a batch of n independent solves (meshes[i], cfgs[i], host initial
  * coefficients coeffs[i]; k may differ between solves, the precision may not).
  * Each solve is set up as by dg_init on the batch's stream (NULL = a stream
- * the batch creates).  A stage of all solves walks a work list of (solve,
- * cell range) chunks in three phases (flux; OE statistics; OE + limiter),
- * in one of two launch forms: 3 = one ordinary launch per phase (default),
- * 1 = one persistent cooperative launch per stage with grid barriers between
- * the phases.  A step is captured as a CUDA graph when the runtime supports
- * it.  Every solve keeps its own alpha, dt, t and OE normalisers, and its
- * results are bitwise those of the same solve run alone, in either form.
+ * the batch creates).  Launch forms: 3 = a stage of all solves walks a work
+ * list of (solve, cell range) chunks in three phases (flux; OE statistics;
+ * OE + limiter), one ordinary launch per phase (default); 1 = the same work
+ * list in one persistent cooperative launch per stage with grid barriers
+ * between the phases; 0 = every solve's own step kernels (those of its
+ * single-solve step graph), the solves as independent branches of one graph
+ * per step, so that small solves run side by side (needs graph support).  A
+ * step is captured as a CUDA graph when the runtime supports it.  Every
+ * solve keeps its own alpha, dt, t and OE normalisers, and its results are
+ * bitwise those of the same solve run alone, in every form.
  * Errors as dg_init; DG_EINVAL if the precisions differ. */
 int32_t dg_batch_create(int32_t n, const dg_mesh *const *meshes, const dg_config *cfgs,
                         const double *const *coeffs, void *cuda_stream, dg_batch **out);
@@ -251,17 +254,20 @@ int32_t dg_batch_sync(dg_batch *batch);
 int32_t dg_batch_solver(dg_batch *batch, int32_t i, dg_solver **out);
 /* launch shape: cells per work chunk (a positive multiple of 128), resident
  * blocks per SM of each launch's grid (clamped per kernel to its occupancy
- * limit) and the launch form (launches per stage: 3 or 1).  DG_EINVAL for
- * another form, or form 1 on a device without cooperative launch.  *grid
- * receives the largest grid of the form's launches. */
+ * limit) and the launch form (3, 1 or 0, as for dg_batch_create; the chunk
+ * and blocks-per-SM values do not apply to form 0).  DG_EINVAL for another
+ * form, or form 1 on a device without cooperative launch; DG_ECUDA when form
+ * 0's graph cannot be built.  *grid receives the largest grid of the form's
+ * launches. */
 int32_t dg_batch_set_shape(dg_batch *batch, int32_t cells_per_block, int32_t blocks_per_sm,
                            int32_t launches_per_stage);
 int32_t dg_batch_shape(const dg_batch *batch, int32_t *cells_per_block, int32_t *blocks_per_sm,
                        int32_t *launches_per_stage, int32_t *grid, int32_t *graph);
-/* Time `steps` steps for both launch forms, every cells-per-chunk in {128,
- * 256, 512, 1024} and every blocks-per-SM up to the occupancy limit, keep the
- * fastest shape and restore every solve's state, time and counters.  The
- * shape changes no result (partials are per 128 cells of each solve). */
+/* Time `steps` steps for form 0 and, for forms 3 and 1, every
+ * cells-per-chunk in {128, 256, 512, 1024} and every blocks-per-SM up to the
+ * occupancy limit; keep the fastest and restore every solve's state, time and
+ * counters.  The shape changes no result (partials are per 128 cells of each
+ * solve). */
 int32_t dg_batch_autotune(dg_batch *batch, int32_t steps, int32_t *best_cells_per_block,
                           int32_t *best_blocks_per_sm, int32_t *best_launches_per_stage,
                           double *best_ms_per_step);

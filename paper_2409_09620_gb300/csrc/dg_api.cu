@@ -770,6 +770,18 @@ void solver_states(const dg_solver *s, StateBuf *un, StateBuf *uh, StateBuf *us)
 int solver_nb(const dg_solver *s) { return s->nb; }
 int32_t solver_read_scalars(const dg_solver *s, Scalars *h) { return read_scalars(s, h); }
 int32_t solver_write_scalars(dg_solver *s, const Scalars *h) { return write_scalars(s, h); }
+int32_t solver_capture_step(dg_solver *s, cudaGraph_t *graph) {
+  *graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return set_error(DG_ECUDA, cudaGetErrorString(e));
+  enqueue_step(s);
+  e = cudaStreamEndCapture(s->stream, graph);
+  if (e != cudaSuccess || !*graph) {
+    cudaGetLastError();
+    return set_error(DG_ECUDA, "step capture failed");
+  }
+  return DG_OK;
+}
 
 int32_t ensure_stack_limit(size_t bytes) {
   size_t cur = 0;

@@ -295,7 +295,8 @@ struct BatchCore {
     return DG_OK;
   }
 
-  // resident blocks per SM of the form's kernels (0: form unavailable)
+  // resident blocks per SM of the form's kernels (0: form unavailable); the
+  // per-solve form (0) runs the solves' own kernels, whose shape is their own
   int max_blocks_per_sm(int f) const {
     return f == 1 ? occ_fused : std::max(occ_phase[0], std::max(occ_phase[1], occ_phase[2]));
   }
@@ -313,6 +314,7 @@ struct BatchCore {
   }
 
   size_t stack_bytes() const {
+    if (form == 0) return 0;   // each solver made room for its own kernels
     if (prec == DG_PREC_MIXED)
       return form == 1 ? kernel_local_bytes(k_batch_stage<float>)
                        : std::max(kernel_local_bytes(k_batch_rk<float>),
@@ -381,12 +383,15 @@ struct BatchCore {
       while (tpw < 8 && tiles / (2 * tpw) >= 2 * resident) tpw *= 2;
       cpb = tpw * TPB;
     }
-    return set_shape(cpb, blocks_per_sm, form);
+    int32_t rc = set_shape(cpb, blocks_per_sm, form);
+    if (rc != DG_OK && form == 0) rc = set_shape(cpb, blocks_per_sm, 3);   // no graph: the phased form
+    return rc;
   }
 
   // work list of chunks of cpb cells (a multiple of TPB), then the step graph
   int32_t set_shape(int cells_per_block, int bpsm, int launch_form) {
-    if (launch_form != 1 && launch_form != 3) return set_error(DG_EINVAL, "launches per stage must be 1 or 3");
+    if (launch_form != 0 && launch_form != 1 && launch_form != 3)
+      return set_error(DG_EINVAL, "launch form must be 0, 1 or 3");
     if (max_blocks_per_sm(launch_form) < 1)
       return set_error(DG_EINVAL, "the device does not support cooperative launches");
     std::vector<WorkItem> work;
@@ -421,6 +426,7 @@ struct BatchCore {
     if (exec) { cudaGraphExecDestroy(exec); exec = nullptr; }
     graph_ok = false;
     if (host_sv.empty()) return DG_OK;
+    if (form == 0) return build_per_solve_graph();
     int32_t rc = ensure_stack_limit(stack_bytes());
     if (rc != DG_OK) return rc;
     cudaGraph_t g = nullptr;
@@ -436,8 +442,35 @@ struct BatchCore {
     return DG_OK;
   }
 
+  // Form 0: every solve's own step (the kernels of its per-solve graph, with
+  // their own registers and occupancy), the solves as independent branches
+  // of one graph, so that the small ones run side by side on the device.
+  // Needs graph support: without it the form is refused.
+  int32_t build_per_solve_graph() {
+    cudaGraph_t g = nullptr;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) return set_error(DG_ECUDA, "graph create");
+    int32_t rc = DG_OK;
+    for (dg_solver *sv_ : solves) {
+      cudaGraph_t child = nullptr;
+      if ((rc = solver_capture_step(sv_, &child)) != DG_OK) break;
+      cudaGraphNode_t node;
+      const cudaError_t e = cudaGraphAddChildGraphNode(&node, g, nullptr, 0, child);
+      cudaGraphDestroy(child);
+      if (e != cudaSuccess) { rc = set_error(DG_ECUDA, cudaGetErrorString(e)); break; }
+    }
+    if (rc == DG_OK && cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) {
+      exec = nullptr;
+      rc = set_error(DG_ECUDA, "per-solve batch graph instantiation failed");
+    }
+    cudaGraphDestroy(g);
+    cudaGetLastError();
+    if (rc == DG_OK) graph_ok = true;
+    return rc;
+  }
+
   int32_t enqueue_steps(int64_t n) {
     if (host_sv.empty()) return DG_OK;
+    if (form == 0 && !graph_ok) return set_error(DG_ECUDA, "the per-solve batch graph is missing");
     for (int64_t s = 0; s < n; ++s) {
       if (graph_ok) {
         if (cudaGraphLaunch(exec, stream) != cudaSuccess) return set_error(DG_ECUDA, "batch graph launch");
@@ -650,11 +683,15 @@ extern "C" int32_t dg_batch_autotune(dg_batch *b, int32_t steps, int32_t *best_c
   double best = INFINITY;
   int bc = core.cpb, bb = core.blocks_per_sm, bf = core.form;
   const int cpbs[4] = {TPB, 2 * TPB, 4 * TPB, 8 * TPB};
-  const int forms[2] = {3, 1};
-  for (int fi = 0; fi < 2; ++fi)
-    for (int ci = 0; ci < 4; ++ci)
-      for (int bpsm = 1; bpsm <= core.max_blocks_per_sm(forms[fi]); ++bpsm) {
-        int32_t rc = core.set_shape(cpbs[ci], bpsm, forms[fi]);
+  // form 0 (per-solve graphs) has no shape of its own: one timing
+  const int forms[3] = {0, 3, 1};
+  for (int fi = 0; fi < 3; ++fi)
+    for (int ci = 0; ci < (forms[fi] == 0 ? 1 : 4); ++ci)
+      for (int bpsm = 1; bpsm <= (forms[fi] == 0 ? 1 : core.max_blocks_per_sm(forms[fi])); ++bpsm) {
+        const int cpb_try = forms[fi] == 0 ? core.cpb : cpbs[ci];
+        const int bpsm_try = forms[fi] == 0 ? core.blocks_per_sm : bpsm;
+        int32_t rc = core.set_shape(cpb_try, bpsm_try, forms[fi]);
+        if (rc != DG_OK && forms[fi] == 0) continue;   // no graph support: the form is unavailable
         if (rc == DG_OK) rc = core.enqueue_steps(1);   // warm-up
         cudaEventRecord(e0, core.stream);
         if (rc == DG_OK) rc = core.enqueue_steps(steps);
@@ -663,7 +700,7 @@ extern "C" int32_t dg_batch_autotune(dg_batch *b, int32_t steps, int32_t *best_c
         if (rc != DG_OK) { free_snaps(); return rc; }
         float ms = 0.0f;
         cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best) { best = ms; bc = cpbs[ci]; bb = bpsm; bf = forms[fi]; }
+        if (ms < best) { best = ms; bc = cpb_try; bb = bpsm_try; bf = forms[fi]; }
       }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -697,6 +734,10 @@ int32_t batch_core_new(int precision, cudaStream_t stream, BatchCore **out) {
   int32_t rc = c->init(precision, stream);
   if (rc != DG_OK) { delete c; return rc; }
   c->auto_chunk = true;
+  // the server's solves run their own step kernels side by side (form 0):
+  // requests of very different sizes keep their own launch shapes, and the
+  // graph is rebuilt only when the set of running solves changes
+  c->form = 0;
   *out = c;
   return DG_OK;
 }

@@ -63,6 +63,9 @@ void solver_states(const dg_solver *s, StateBuf *un, StateBuf *uh, StateBuf *us)
 int solver_nb(const dg_solver *s);
 int32_t solver_read_scalars(const dg_solver *s, Scalars *h);
 int32_t solver_write_scalars(dg_solver *s, const Scalars *h);
+// one SSP-RK3 step of the solver (the kernels of its own step graph) captured
+// into a new graph, which the caller destroys
+int32_t solver_capture_step(dg_solver *s, cudaGraph_t *graph);
 
 // the mesh's device arrays as the kernels see them; boundary tags usable by
 // the scalar solver (dg_api.cu)

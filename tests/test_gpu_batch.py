@@ -1,7 +1,8 @@
 """GPU tests of batches: independent ragged meshes (P1 and P2 mixed) advanced
-together, by one launch per phase or by one persistent cooperative launch per
-RK stage.  Each solve of a batch must be bitwise identical to the same solve
-advanced alone, for either launch form and any launch shape, with per-solve
+together, by one launch per phase, by one persistent cooperative launch per
+RK stage, or by the solves' own step kernels as parallel branches of one
+graph.  Each solve of a batch must be bitwise identical to the same solve
+advanced alone, for every launch form and any launch shape, with per-solve
 end times, in FP64 and in the mixed form; and each solve must match the CPU
 oracle advanced from the same state (FP64: 1e-9 relative after several
 steps; mixed form: the tolerances of the mixed-form tests)."""
@@ -60,7 +61,7 @@ def _setup(N, wls, precision, O=None):
     return meshes, cfgs, us
 
 
-@pytest.mark.parametrize("form", [3, 1])
+@pytest.mark.parametrize("form", [3, 1, 0])
 @pytest.mark.parametrize("precision", [0, 1])
 def test_batch_equals_solo(oracle_mod, N, precision, form):
     wls = _workloads()
@@ -90,9 +91,11 @@ def test_batch_end_times_and_shapes(oracle_mod, N):
     t_end = np.array([0.002, 0.0005, 0.003, 0.0002, 0.001])
     batch.set_shape(256, 1)
     st = batch.advance(t_end, max_steps=2)
-    batch.set_shape(128, 2, 1)       # change the launch form part-way
-    st2 = batch.advance(t_end)
-    st = [dict(a, steps=a["steps"] + b["steps"]) for a, b in zip(st, st2)]
+    batch.set_shape(128, 2, 1)       # change the launch form part-way, twice
+    st2 = batch.advance(t_end, max_steps=2)
+    batch.set_shape(128, 2, 0)
+    st3 = batch.advance(t_end)
+    st = [dict(a, steps=a["steps"] + b["steps"] + c["steps"]) for a, b, c in zip(st, st2, st3)]
     for i in range(len(wls)):
         solo = N.Solver(meshes[i], cfgs[i], us[i])
         sst, _ = solo.advance(t_end[i])
@@ -113,7 +116,7 @@ def test_batch_autotune_restores_state(N):
     best = batch.autotune(steps=2)
     shape = batch.shape()
     assert best["cells_per_block"] == shape["cells_per_block"] and best["ms_per_step"] > 0
-    assert best["launches_per_stage"] == shape["launches_per_stage"] in (1, 3)
+    assert best["launches_per_stage"] == shape["launches_per_stage"] in (0, 1, 3)
     after = [batch.solver(i).get_state() for i in range(len(wls))]
     for (a, ta), (b, tb) in zip(before, after):
         assert ta == tb and np.array_equal(a, b)

@@ -120,11 +120,11 @@ def test_periodic_two_by_two_rejected(oracle_mod, N):
         oracle_mod.OracleMesh.from_mesh(wl.mesh)
 
 
-@pytest.mark.parametrize("form", [3, 1])
+@pytest.mark.parametrize("form", [3, 1, 0])
 @pytest.mark.parametrize("precision", [0, 1])
 def test_degenerate_meshes_in_a_batch(oracle_mod, N, precision, form):
     """A batch of the tiny meshes (1, 2, 8 and 132 cells, P1 and P2) is
-    bitwise the solves run alone, in both launch forms, and matches the
+    bitwise the solves run alone, in every launch form, and matches the
     oracle."""
     from tests.test_gpu_batch import check_against_oracle
     wls = [_case("one_cell", 1), _case("two_cells", 2), _case("dmr_8", 2), _case("two_tiles_ragged", 1)]
