@@ -341,8 +341,10 @@ class _SolverView(Solver):
 
 
 class Batch:
-    """dg_batch handle: independent solves advanced together over one work list,
-    one launch per phase (form 3) or one cooperative launch per stage (form 1)."""
+    """dg_batch handle: independent solves advanced together, over one work
+    list with one launch per phase (form 3) or one cooperative launch per stage
+    (form 1), or as the solves' own step kernels in parallel branches of one
+    graph per step (form 0)."""
 
     def __init__(self, meshes, cfgs, coeffs, stream=None):
         n = len(meshes)
